@@ -1,0 +1,106 @@
+/* qstar: the Pfaffian-sign hot path for QCD+QED with C* boundary conditions
+ * (arXiv:2108.11989, Sec. 3), as a C-ABI library for one NVIDIA GB300 GPU.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Lattice.  The physical lattice is T x L^3 with C* boundary conditions in the
+ *   spatial directions and periodic (or antiperiodic) time.  The quark/antiquark
+ *   doublet on which D acts (a 24V x 24V matrix, Sec. 3) is stored on the
+ *   orientifold-doubled lattice T x L x L x 2L: sites with x in [0, L) hold psi,
+ *   sites with x in [L, 2L) hold psi^C.  Moving across the y (or z) boundary moves
+ *   x by L; x itself is periodic with period 2L.  N_s = 2 L^3 T doubled sites.
+ * Directions.  mu = 0 (t), 1 (x), 2 (y), 3 (z).
+ * Dirac basis.  Chiral basis, gamma_5 = diag(1, 1, -1, -1), C = i gamma_0 gamma_2.
+ * Spinor layout ("canonical").  [rhs][t][z][y][x in 0..2L-1][spin 4][colour 3][re, im],
+ *   double for QS_F64, float for QS_F32.  Buffers given to the apply calls are
+ *   DEVICE pointers owned by the caller; in and out must not overlap.
+ * Gauge layout (host input).  su3 [t][z][y][x in 0..L-1][mu 4][a 3][b 3][re, im]
+ *   (physical lattice only, double); u1_theta [t][z][y][x][mu] (double) or NULL.
+ *   The mirror half is derived inside (charge conjugate links).
+ * Operator (Sec. 2: O(a)-improved Wilson quarks with SU(3) and U(1) SW terms;
+ *   Sec. 3: Q = gamma_5 D):
+ *     D psi(x) = (4 + m0) psi(x) + A(x) psi(x)
+ *                - 1/2 sum_mu [ V(x,mu)(1 - gamma_mu) psi(x+mu) + V(x-mu,mu)^+ (1 + gamma_mu) psi(x-mu) ]
+ *     V = U exp(i theta),  A = (i/4) sum_{mu,nu} sigma_{mu nu} (c_sw F^SU3 + c_sw,U1 F^U1),
+ *     F = clover field strength (Q_{mu nu} - Q_{nu mu}) / 8.
+ *
+ * Errors.  Every call returns 0 (QS_OK) or a negative code below; none aborts the
+ *   process.  On error the contents of output buffers are unspecified.
+ *   qs_strerror() gives a static message.
+ * Streams.  All GPU work of a lattice handle runs on the stream given at creation
+ *   (NULL = the legacy default stream).  Calls on one handle must not overlap.
+ * No CPU fallback: a call that cannot run on the GPU returns QS_ECUDA.
+ */
+#ifndef QSTAR_H
+#define QSTAR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QS_API __attribute__((visibility("default")))
+#else
+#define QS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum qs_status {
+    QS_OK = 0,
+    QS_EINVAL = -1,      /* bad argument (size, pointer, precision, call order) */
+    QS_ENOMEM = -2,      /* device allocation failed */
+    QS_ECUDA = -3,       /* CUDA runtime error (message in qs_last_cuda_error) */
+    QS_ENOCONV = -4,     /* an iteration hit its cap before reaching its tolerance */
+    QS_ETIMEOUT = -5,    /* a bounded device wait gave up */
+    QS_ENUMERIC = -6,    /* NaN / Inf met in a reduction */
+    QS_EUNDECIDED = -7   /* |lambda| at the target mass is below its certified accuracy */
+};
+
+enum qs_prec { QS_F64 = 0, QS_F32 = 1 };
+
+typedef struct qs_lattice qs_lattice;
+
+typedef struct {
+    int L, T;            /* physical extents; L even, L >= 2, T >= 2 */
+    int cstar_mask;      /* bit k-1: C* in spatial direction k (bit 0 = x, required) */
+    int t_antiperiodic;  /* 0: periodic in time (Sec. 2), 1: antiperiodic for fermions */
+    int device;          /* CUDA device ordinal */
+} qs_geom;
+
+/* Create a lattice handle (Sec. 3 geometry).  stream: a cudaStream_t or NULL.
+ * Allocates nothing large until qs_load_gauge.  *out receives the handle. */
+QS_API int qs_create_lattice(const qs_geom *geom, void *stream, qs_lattice **out);
+
+/* Release every device buffer of the handle.  NULL is accepted. */
+QS_API int qs_destroy_lattice(qs_lattice *lat);
+
+/* Number of doubled sites N_s = 2 L^3 T (0 for a NULL handle). */
+QS_API int64_t qs_n_sites(const qs_lattice *lat);
+
+/* Load a gauge configuration (Sec. 2: SU(3) x U(1) links, c_sw's) from HOST arrays
+ * (layouts above; copied, the caller keeps ownership), build the doubled links and
+ * the SW term A(x) on the GPU in FP64, and keep FP64 and FP32 copies resident.
+ * Replaces any earlier configuration of the handle.  Synchronises the stream. */
+QS_API int qs_load_gauge(qs_lattice *lat, const double *su3, const double *u1_theta,
+                  double csw_su3, double csw_u1);
+
+/* out = D(m0) in for nrhs vectors (Sec. 2 operator on the doubled lattice, Sec. 3).
+ * in, out: device buffers of nrhs * N_s * 24 reals, canonical layout, in precision
+ * prec (QS_F64: double, arithmetic in FP64; QS_F32: float, arithmetic in FP32).
+ * Asynchronous on the handle's stream. */
+QS_API int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec);
+
+/* out = Q(m0) in = gamma_5 D(m0) in (Sec. 3).  Same arguments as qs_apply_Dw. */
+QS_API int qs_apply_Q(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec);
+
+/* Static description of a status code. */
+QS_API const char *qs_strerror(int status);
+
+/* Text of the last CUDA error seen by the library in this process ("" if none). */
+QS_API const char *qs_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSTAR_H */

@@ -35,37 +35,35 @@ def _dag(U):
     return np.conj(np.swapaxes(U, -1, -2))
 
 
-def plaquette_leaves(lat, U, mu, nu):
+def plaquette_leaves(lat, U, mu, nu, sites=None):
     """Q_{mu nu}(x): sum of the four plaquette leaves at x in the (mu, nu) plane.
 
-    U has shape (n_sites, 4, n, n) (n = 3 for SU(3), n = 1 for U(1) phases).
+    U has shape (n_sites, 4, n, n) (n = 3 for SU(3), n = 1 for U(1) phases);
+    ``sites`` selects the sites x (default: all).
     """
-    xpm, _ = lat.neighbour(mu, +1)
-    xmm, _ = lat.neighbour(mu, -1)
-    xpn, _ = lat.neighbour(nu, +1)
-    xmn, _ = lat.neighbour(nu, -1)
-    nbr_nu_p = lambda idx: lat.neighbour(nu, +1)[0][idx]
-    nbr_nu_m = lambda idx: lat.neighbour(nu, -1)[0][idx]
-    nbr_mu_p = lambda idx: lat.neighbour(mu, +1)[0][idx]
-    xmm_pn = nbr_nu_p(xmm)      # x - mu + nu
-    xmm_mn = nbr_nu_m(xmm)      # x - mu - nu
-    xmn_pm = nbr_mu_p(xmn)      # x - nu + mu
+    x = np.arange(lat.n_sites) if sites is None else np.asarray(sites)
+    fmu, bmu = lat.neighbour(mu, +1)[0], lat.neighbour(mu, -1)[0]
+    fnu, bnu = lat.neighbour(nu, +1)[0], lat.neighbour(nu, -1)[0]
+    xpm, xmm, xpn, xmn = fmu[x], bmu[x], fnu[x], bnu[x]
+    xmm_pn = fnu[xmm]      # x - mu + nu
+    xmm_mn = bnu[xmm]      # x - mu - nu
+    xmn_pm = fmu[xmn]      # x - nu + mu
     Um, Un = U[:, mu], U[:, nu]
-    leaf1 = Um @ Un[xpm] @ _dag(Um[xpn]) @ _dag(Un)
-    leaf2 = Un @ _dag(Um[xmm_pn]) @ _dag(Un[xmm]) @ Um[xmm]
+    leaf1 = Um[x] @ Un[xpm] @ _dag(Um[xpn]) @ _dag(Un[x])
+    leaf2 = Un[x] @ _dag(Um[xmm_pn]) @ _dag(Un[xmm]) @ Um[xmm]
     leaf3 = _dag(Um[xmm]) @ _dag(Un[xmm_mn]) @ Um[xmm_mn] @ Un[xmn]
-    leaf4 = _dag(Un[xmn]) @ Um[xmn] @ Un[xmn_pm] @ _dag(Um)
+    leaf4 = _dag(Un[xmn]) @ Um[xmn] @ Un[xmn_pm] @ _dag(Um[x])
     return leaf1 + leaf2 + leaf3 + leaf4
 
 
-def field_strength(lat, U, mu, nu):
+def field_strength(lat, U, mu, nu, sites=None):
     """Clover field strength F_{mu nu} = (Q_{mu nu} - Q_{nu mu}) / 8."""
-    return (plaquette_leaves(lat, U, mu, nu) - plaquette_leaves(lat, U, nu, mu)) / 8.0
+    return (plaquette_leaves(lat, U, mu, nu, sites) - plaquette_leaves(lat, U, nu, mu, sites)) / 8.0
 
 
-def clover_term(lat, U3, theta, csw_su3, csw_u1):
-    """A(x) = (i/4) sum_{mu,nu} sigma_{mu nu} (c_sw F^SU3 + c_sw,U1 F^U1), shape (n_sites, 12, 12)."""
-    n = lat.n_sites
+def clover_term(lat, U3, theta, csw_su3, csw_u1, sites=None):
+    """A(x) = (i/4) sum_{mu,nu} sigma_{mu nu} (c_sw F^SU3 + c_sw,U1 F^U1), shape (n, 12, 12)."""
+    n = lat.n_sites if sites is None else len(sites)
     A = np.zeros((n, 12, 12), dtype=np.complex128)
     phase = np.exp(1j * theta)[:, :, None, None]
     I3 = np.eye(3)
@@ -73,41 +71,55 @@ def clover_term(lat, U3, theta, csw_su3, csw_u1):
         for nu in range(4):
             if mu == nu:
                 continue
-            F = csw_su3 * field_strength(lat, U3, mu, nu)
+            F = csw_su3 * field_strength(lat, U3, mu, nu, sites)
             if csw_u1 != 0.0:
-                F = F + csw_u1 * field_strength(lat, phase, mu, nu)[:, 0, 0][:, None, None] * I3
+                F = F + csw_u1 * field_strength(lat, phase, mu, nu, sites)[:, 0, 0][:, None, None] * I3
             A += 0.25j * np.einsum("ab,xij->xaibj", SIGMA[mu, nu], F).reshape(n, 12, 12)
     return A
 
 
 class WilsonDirac:
-    """The operator for one gauge configuration (synth_inputs.GaugeConfig)."""
+    """The operator for one gauge configuration (synth_inputs.GaugeConfig).
 
-    def __init__(self, cfg):
+    With ``lazy=True`` the site blocks are built only for the output sites asked
+    for (used for sampled checks on large lattices)."""
+
+    def __init__(self, cfg, lazy=False):
         self.cfg = cfg
         self.lat = DoubledLattice(cfg.T, cfg.L, cfg.cstar_mask, cfg.t_antiperiodic)
         lat = self.lat
         self.U3, self.theta = lat.doubled_links(cfg.su3, cfg.theta)
         self.V = self.U3 * np.exp(1j * self.theta)[:, :, None, None]
-        self.A = clover_term(lat, self.U3, self.theta, cfg.csw_su3, cfg.csw_u1)
         self.n = 12 * lat.n_sites
-        # neighbour columns and 12x12 blocks at m0 = 0: slot 0 diagonal, 1+2mu fwd, 2+2mu bwd
-        ns = lat.n_sites
-        self.cols = np.zeros((ns, 9), dtype=np.int64)
-        self.blocks = np.zeros((ns, 9, 12, 12), dtype=np.complex128)
-        self.cols[:, 0] = np.arange(ns)
-        self.blocks[:, 0] = 4.0 * np.eye(12) + self.A
+        self.nbr = [(lat.neighbour(mu, +1), lat.neighbour(mu, -1)) for mu in range(4)]
+        self.lazy = lazy
+        if not lazy:
+            self.A = clover_term(lat, self.U3, self.theta, cfg.csw_su3, cfg.csw_u1)
+            self.cols, self.blocks = self.site_blocks(np.arange(lat.n_sites), self.A)
+
+    def site_blocks(self, sites, A=None):
+        """Neighbour columns and 12x12 blocks of D(m0 = 0) for output ``sites``:
+        slot 0 diagonal (4 + A), slot 1 + 2 mu forward hop, slot 2 + 2 mu backward hop."""
+        s = np.asarray(sites)
+        ns = len(s)
+        if A is None:
+            A = clover_term(self.lat, self.U3, self.theta, self.cfg.csw_su3, self.cfg.csw_u1, s)
+        cols = np.zeros((ns, 9), dtype=np.int64)
+        blocks = np.zeros((ns, 9, 12, 12), dtype=np.complex128)
+        cols[:, 0] = s
+        blocks[:, 0] = 4.0 * np.eye(12) + A
         for mu in range(4):
-            fw, bcf = lat.neighbour(mu, +1)
-            bw, bcb = lat.neighbour(mu, -1)
-            self.cols[:, 1 + 2 * mu] = fw
-            self.cols[:, 2 + 2 * mu] = bw
+            (fw, bcf), (bw, bcb) = self.nbr[mu]
+            fw, bcf, bw, bcb = fw[s], bcf[s], bw[s], bcb[s]
+            cols[:, 1 + 2 * mu] = fw
+            cols[:, 2 + 2 * mu] = bw
             Pm = ID4 - GAMMA[mu]
             Pp = ID4 + GAMMA[mu]
-            self.blocks[:, 1 + 2 * mu] = -0.5 * bcf[:, None, None] * np.einsum(
-                "ab,xij->xaibj", Pm, self.V[:, mu]).reshape(ns, 12, 12)
-            self.blocks[:, 2 + 2 * mu] = -0.5 * bcb[:, None, None] * np.einsum(
+            blocks[:, 1 + 2 * mu] = -0.5 * bcf[:, None, None] * np.einsum(
+                "ab,xij->xaibj", Pm, self.V[s, mu]).reshape(ns, 12, 12)
+            blocks[:, 2 + 2 * mu] = -0.5 * bcb[:, None, None] * np.einsum(
                 "ab,xij->xaibj", Pp, _dag(self.V[bw, mu])).reshape(ns, 12, 12)
+        return cols, blocks
 
     # ---- matrix-free -------------------------------------------------------
     def apply_D(self, psi, m0, sites=None):
@@ -115,9 +127,13 @@ class WilsonDirac:
         given, only those output sites are computed (shape (len(sites), 12))."""
         p = psi.reshape(-1, 12)
         s = np.arange(self.lat.n_sites) if sites is None else np.asarray(sites)
+        if self.lazy:
+            cols, blocks = self.site_blocks(s)
+        else:
+            cols, blocks = self.cols[s], self.blocks[s]
         out = m0 * p[s]
         for j in range(9):
-            out = out + np.einsum("xij,xj->xi", self.blocks[s, j], p[self.cols[s, j]])
+            out = out + np.einsum("xij,xj->xi", blocks[:, j], p[cols[:, j]])
         return out if sites is not None else out.reshape(psi.shape)
 
     def apply_Q(self, psi, m0, sites=None):

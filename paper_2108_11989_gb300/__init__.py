@@ -1,0 +1,145 @@
+"""Python binding of libqstar (include/qstar.h): argument marshalling only.
+
+Every function here forwards to the C-ABI entry point of the same name (without
+the ``qs_`` prefix); device buffers are torch tensors (their data pointers are
+passed through), host inputs are numpy arrays.  There is no fallback: if the
+CUDA library is not built or not loadable, importing this package raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+__all__ = ["QStarError", "Lattice", "create_lattice", "load_gauge", "apply_Dw", "apply_Q",
+           "strerror", "QS_F64", "QS_F32", "lib"]
+
+QS_F64, QS_F32 = 0, 1
+
+
+class QStarError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = _lib.qs_strerror(code).decode()
+        cu = _lib.qs_last_cuda_error().decode()
+        super().__init__(f"{where}: {msg} ({code})" + (f" [{cu}]" if code == -3 and cu else ""))
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("cstar_mask", ctypes.c_int),
+                ("t_antiperiodic", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB):
+        raise ImportError(f"libqstar.so is not built ({LIB}); run __graft_entry__.build() "
+                          "or python -m paper_2108_11989_gb300.build")
+    lib = ctypes.CDLL(LIB)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "qs_create_lattice": (I, [ctypes.POINTER(_Geom), P, ctypes.POINTER(P)]),
+        "qs_destroy_lattice": (I, [P]),
+        "qs_n_sites": (ctypes.c_int64, [P]),
+        "qs_load_gauge": (I, [P, P, P, D, D]),
+        "qs_apply_Dw": (I, [P, D, P, P, I, I]),
+        "qs_apply_Q": (I, [P, D, P, P, I, I]),
+        "qs_strerror": (ctypes.c_char_p, [I]),
+        "qs_last_cuda_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+_lib = _load()
+lib = _lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise QStarError(code, where)
+
+
+def strerror(code):
+    return _lib.qs_strerror(code).decode()
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.float64:
+        return QS_F64
+    if t.dtype == torch.float32:
+        return QS_F32
+    raise TypeError(f"unsupported spinor dtype {t.dtype}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def create_lattice(L, T, cstar_mask=0b111, t_antiperiodic=False, device=0, stream=None):
+    """qs_create_lattice; returns the opaque handle (ctypes.c_void_p)."""
+    g = _Geom(L, T, cstar_mask, int(bool(t_antiperiodic)), device)
+    h = ctypes.c_void_p()
+    _check(_lib.qs_create_lattice(ctypes.byref(g), _stream_ptr(stream), ctypes.byref(h)), "create_lattice")
+    return h
+
+
+def load_gauge(h, su3, theta, csw_su3, csw_u1):
+    """qs_load_gauge from host numpy arrays su3[T,L,L,L,4,3,3] complex128, theta[T,L,L,L,4] or None."""
+    su3 = np.ascontiguousarray(su3, dtype=np.complex128)
+    th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+    _check(_lib.qs_load_gauge(h, su3.ctypes.data, None if th is None else th.ctypes.data,
+                              float(csw_su3), float(csw_u1)), "load_gauge")
+
+
+def _nrhs(h, t):
+    ns = _lib.qs_n_sites(h)
+    n = t.numel() // (ns * 24)
+    if n * ns * 24 != t.numel():
+        raise ValueError("spinor size is not a multiple of N_s * 24 reals")
+    return n
+
+
+def apply_Dw(h, m0, inp, out):
+    """qs_apply_Dw on device tensors (float64 or float32, canonical layout)."""
+    _check(_lib.qs_apply_Dw(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
+                            _prec_of(inp)), "apply_Dw")
+
+
+def apply_Q(h, m0, inp, out):
+    _check(_lib.qs_apply_Q(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
+                           _prec_of(inp)), "apply_Q")
+
+
+class Lattice:
+    """Owning wrapper around a qs_lattice handle."""
+
+    def __init__(self, L, T, cstar_mask=0b111, t_antiperiodic=False, device=0, stream=None):
+        self.L, self.T = L, T
+        self.h = create_lattice(L, T, cstar_mask, t_antiperiodic, device, stream)
+        self.n_sites = _lib.qs_n_sites(self.h)
+
+    def load_gauge(self, su3, theta, csw_su3, csw_u1):
+        load_gauge(self.h, su3, theta, csw_su3, csw_u1)
+
+    def apply_Dw(self, m0, inp, out):
+        apply_Dw(self.h, m0, inp, out)
+
+    def apply_Q(self, m0, inp, out):
+        apply_Q(self.h, m0, inp, out)
+
+    def close(self):
+        if self.h is not None:
+            _lib.qs_destroy_lattice(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

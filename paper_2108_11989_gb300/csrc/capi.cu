@@ -1,0 +1,135 @@
+// C-ABI entry points: lattice handles, operator application, status strings.
+#include "qs_internal.cuh"
+#include "dslash.cuh"
+
+#include <stdio.h>
+#include <stdlib.h>
+
+static char g_last_cuda_error[256] = "";
+
+void qs_record_cuda_error(cudaError_t e, const char *where)
+{
+    snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
+Geom qs_make_geom(int L, int T, int cstar_mask, int t_anti)
+{
+    Geom g;
+    g.L = L; g.T = T; g.L2 = 2 * L;
+    g.cstar_y = (cstar_mask >> 1) & 1;
+    g.cstar_z = (cstar_mask >> 2) & 1;
+    g.t_anti = t_anti ? 1 : 0;
+    g.sy = g.L2;
+    g.sz = (int64_t)g.L2 * L;
+    g.st = (int64_t)g.L2 * L * L;
+    g.Ns = g.st * T;
+    g.Vphys = g.Ns / 2;
+    return g;
+}
+
+void qs_free_gauge(qs_lattice *lat);
+void qs_free_workspace(qs_lattice *lat);
+
+extern "C" int qs_create_lattice(const qs_geom *geom, void *stream, qs_lattice **out)
+{
+    if (!geom || !out) return QS_EINVAL;
+    *out = nullptr;
+    if (geom->L < 2 || (geom->L & 1) || geom->T < 2 || !(geom->cstar_mask & 1) ||
+        geom->cstar_mask < 0 || geom->cstar_mask > 7)
+        return QS_EINVAL;
+    // index arithmetic is 64-bit; keep N_s * 24 below 2^62
+    if ((double)geom->L * geom->L * geom->L * geom->T * 48.0 > 4.0e18) return QS_EINVAL;
+    int ndev = 0;
+    QS_CUDA(cudaGetDeviceCount(&ndev));
+    if (geom->device < 0 || geom->device >= ndev) return QS_EINVAL;
+    QS_CUDA(cudaSetDevice(geom->device));
+    qs_lattice *lat = (qs_lattice *)calloc(1, sizeof(qs_lattice));
+    if (!lat) return QS_ENOMEM;
+    lat->g = qs_make_geom(geom->L, geom->T, geom->cstar_mask, geom->t_antiperiodic);
+    lat->device = geom->device;
+    lat->stream = (cudaStream_t)stream;
+    *out = lat;
+    return QS_OK;
+}
+
+extern "C" int qs_destroy_lattice(qs_lattice *lat)
+{
+    if (!lat) return QS_OK;
+    cudaSetDevice(lat->device);
+    qs_free_gauge(lat);
+    qs_free_workspace(lat);
+    free(lat);
+    return QS_OK;
+}
+
+extern "C" int64_t qs_n_sites(const qs_lattice *lat) { return lat ? lat->g.Ns : 0; }
+
+int qs_apply_op(qs_lattice *lat, const double *m0, const void *in, void *out, int nrhs, int prec,
+                int gamma5)
+{
+    if (!lat || !in || !out || nrhs < 1 || nrhs > QS_MAX_RHS) return QS_EINVAL;
+    if (!lat->gauge_loaded) return QS_EINVAL;
+    if (in == out) return QS_EINVAL;
+    size_t bytes = (size_t)nrhs * lat->g.Ns * 24 * (prec == QS_F64 ? 8 : 4);
+    const char *a = (const char *)in, *b = (const char *)out;
+    if (a < b + bytes && b < a + bytes) return QS_EINVAL;      // overlap
+    if (((uintptr_t)in | (uintptr_t)out) & 15) return QS_EINVAL; // vector loads need 16 B
+    QS_CUDA(cudaSetDevice(lat->device));
+    cudaError_t e;
+    if (prec == QS_F64) {
+        DslashArgs<double> d;
+        d.g = lat->g; d.links = lat->links64; d.clov = lat->clov64;
+        d.in = (const double *)in; d.out = (double *)out; d.gamma5 = gamma5;
+        for (int r = 0; r < nrhs; ++r) d.m0[r] = m0[r];
+        e = qs_dslash_launch<double>(d, nrhs, lat->stream);
+    } else if (prec == QS_F32) {
+        DslashArgs<float> d;
+        d.g = lat->g; d.links = lat->links32; d.clov = lat->clov32;
+        d.in = (const float *)in; d.out = (float *)out; d.gamma5 = gamma5;
+        for (int r = 0; r < nrhs; ++r) d.m0[r] = m0[r];
+        e = qs_dslash_launch<float>(d, nrhs, lat->stream);
+    } else {
+        return QS_EINVAL;
+    }
+    if (e != cudaSuccess) {
+        qs_record_cuda_error(e, "dslash launch");
+        return QS_ECUDA;
+    }
+    return QS_OK;
+}
+
+extern "C" int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec)
+{
+    double m[QS_MAX_RHS];
+    if (nrhs < 1 || nrhs > QS_MAX_RHS) return QS_EINVAL;
+    for (int r = 0; r < nrhs; ++r) m[r] = m0;
+    return qs_apply_op(lat, m, in, out, nrhs, prec, 0);
+}
+
+extern "C" int qs_apply_Q(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec)
+{
+    double m[QS_MAX_RHS];
+    if (nrhs < 1 || nrhs > QS_MAX_RHS) return QS_EINVAL;
+    for (int r = 0; r < nrhs; ++r) m[r] = m0;
+    return qs_apply_op(lat, m, in, out, nrhs, prec, 1);
+}
+
+extern "C" const char *qs_strerror(int status)
+{
+    switch (status) {
+    case QS_OK: return "ok";
+    case QS_EINVAL: return "invalid argument";
+    case QS_ENOMEM: return "device allocation failed";
+    case QS_ECUDA: return "CUDA runtime error";
+    case QS_ENOCONV: return "iteration cap reached before the tolerance";
+    case QS_ETIMEOUT: return "bounded device wait gave up";
+    case QS_ENUMERIC: return "NaN or Inf in a reduction";
+    case QS_EUNDECIDED: return "|lambda| at the target mass is below its certified accuracy";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *qs_last_cuda_error(void) { return g_last_cuda_error; }
+
+// workspace of the solvers (none yet)
+void qs_free_workspace(qs_lattice *lat) { (void)lat; }

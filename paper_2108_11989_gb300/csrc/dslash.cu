@@ -1,0 +1,314 @@
+// The O(a)-improved Wilson-Dirac operator D and Q = gamma_5 D on the C*-doubled
+// lattice (Sec. 2 operator, Sec. 3 doublet and Q).  One thread per doubled site;
+// each thread forms
+//   out = (4 + m0) psi + A psi - 1/2 sum_mu [ V (1 - g_mu) psi(x+mu) + V^+ (1 + g_mu) psi(x-mu) ]
+// and, for Q, flips the sign of spins 2, 3.  (1 -+ g_mu) has rank 2: in the
+// chiral basis g_mu = [[0, e_mu], [e_mu^+, 0]] (e_0 = -1, e_k = -i s_k), so
+//   (1 - g_mu) psi = (h, -e_mu^+ h),  h = psi_up - e_mu psi_dn,
+//   (1 + g_mu) psi = (h, +e_mu^+ h),  h = psi_up + e_mu psi_dn,
+// and only the half spinor h is multiplied by the link.
+#include "qs_internal.cuh"
+#include "dslash.cuh"
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ void load24(const R *__restrict__ p, R v[24]);
+template <>
+__device__ __forceinline__ void load24<float>(const float *__restrict__ p, float v[24])
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float4 a = __ldg(q + i);
+        v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
+    }
+}
+template <>
+__device__ __forceinline__ void load24<double>(const double *__restrict__ p, double v[24])
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        double2 a = __ldg(q + i);
+        v[2 * i] = a.x; v[2 * i + 1] = a.y;
+    }
+}
+template <typename R>
+__device__ __forceinline__ void store24(R *__restrict__ p, const R v[24]);
+template <>
+__device__ __forceinline__ void store24<float>(float *__restrict__ p, const float v[24])
+{
+    float4 *q = reinterpret_cast<float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+template <>
+__device__ __forceinline__ void store24<double>(double *__restrict__ p, const double v[24])
+{
+    double2 *q = reinterpret_cast<double2 *>(p);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
+}
+
+template <typename R>
+__device__ __forceinline__ C2<R> sp(const R v[24], int s, int c)
+{
+    return cmk(v[(s * 3 + c) * 2], v[(s * 3 + c) * 2 + 1]);
+}
+
+// half spinor h for direction MU, forward (FW = true: 1 - g) or backward (1 + g)
+template <int MU, bool FW, typename R>
+__device__ __forceinline__ void project(const R v[24], C2<R> h[2][3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        C2<R> p0 = sp(v, 0, c), p1 = sp(v, 1, c), p2 = sp(v, 2, c), p3 = sp(v, 3, c);
+        if (MU == 0) {
+            h[0][c] = FW ? p0 + p2 : p0 - p2;
+            h[1][c] = FW ? p1 + p3 : p1 - p3;
+        } else if (MU == 1) {
+            h[0][c] = FW ? p0 + mul_i(p3) : p0 - mul_i(p3);
+            h[1][c] = FW ? p1 + mul_i(p2) : p1 - mul_i(p2);
+        } else if (MU == 2) {
+            h[0][c] = FW ? p0 + p3 : p0 - p3;
+            h[1][c] = FW ? p1 - p2 : p1 + p2;
+        } else {
+            h[0][c] = FW ? p0 + mul_i(p2) : p0 - mul_i(p2);
+            h[1][c] = FW ? p1 - mul_i(p3) : p1 + mul_i(p3);
+        }
+    }
+}
+
+// acc += (chi, lower(chi)) with lower = -+ e_mu^+ chi
+template <int MU, bool FW, typename R>
+__device__ __forceinline__ void reconstruct(C2<R> acc[12], const C2<R> x[2][3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = acc[c] + x[0][c];
+        acc[3 + c] = acc[3 + c] + x[1][c];
+        C2<R> l2, l3;
+        if (MU == 0) {
+            l2 = FW ? x[0][c] : cmk(-x[0][c].re, -x[0][c].im);
+            l3 = FW ? x[1][c] : cmk(-x[1][c].re, -x[1][c].im);
+        } else if (MU == 1) {
+            C2<R> a = mul_i(x[1][c]), b = mul_i(x[0][c]);
+            l2 = FW ? cmk(-a.re, -a.im) : a;
+            l3 = FW ? cmk(-b.re, -b.im) : b;
+        } else if (MU == 2) {
+            l2 = FW ? cmk(-x[1][c].re, -x[1][c].im) : x[1][c];
+            l3 = FW ? x[0][c] : cmk(-x[0][c].re, -x[0][c].im);
+        } else {
+            C2<R> a = mul_i(x[0][c]), b = mul_i(x[1][c]);
+            l2 = FW ? cmk(-a.re, -a.im) : a;
+            l3 = FW ? b : cmk(-b.re, -b.im);
+        }
+        acc[6 + c] = acc[6 + c] + l2;
+        acc[9 + c] = acc[9 + c] + l3;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_link(const typename LinkT<R>::T *__restrict__ links, int64_t Vp, int mu,
+                                          int64_t p, C2<R> U[9])
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        typename LinkT<R>::T a = __ldg(links + (int64_t)(mu * 9 + k) * Vp + p);
+        U[k] = cmk(a.x, a.y);
+    }
+}
+
+// chi = W h for W = U (conj = false) or U^* (conj = true)
+template <typename R>
+__device__ __forceinline__ void mul_link(const C2<R> U[9], bool cj, const C2<R> h[2][3], C2<R> x[2][3])
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            C2<R> r = cmk(R(0), R(0));
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                C2<R> u = cj ? conjc(U[a * 3 + b]) : U[a * 3 + b];
+                r = r + u * h[s][b];
+            }
+            x[s][a] = r;
+        }
+}
+
+// chi = W^+ h for W = U (conj = false) or U^* (conj = true)
+template <typename R>
+__device__ __forceinline__ void mul_link_dag(const C2<R> U[9], bool cj, const C2<R> h[2][3], C2<R> x[2][3])
+{
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            C2<R> r = cmk(R(0), R(0));
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                C2<R> u = cj ? U[b * 3 + a] : conjc(U[b * 3 + a]);
+                r = r + u * h[s][b];
+            }
+            x[s][a] = r;
+        }
+}
+
+template <int MU, typename R, int NRHS>
+__device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, int64_t s, int64_t p, bool mir,
+                                        C2<R> acc[NRHS][12])
+{
+    const Geom &g = a.g;
+    C2<R> U[9];
+    int sg;
+    // forward: V(x, mu) (1 - g_mu) psi(x + mu)
+    {
+        int64_t sf = qs_nbr(g, s, MU, +1, &sg);
+        load_link<R>(a.links, g.Vphys, MU, p, U);
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) {
+            R v[24];
+            load24<R>(a.in + ((int64_t)r * g.Ns + sf) * 24, v);
+            C2<R> h[2][3], x[2][3];
+            project<MU, true, R>(v, h);
+            mul_link<R>(U, mir, h, x);
+            if (MU == 0 && sg < 0) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) x[q][c] = cmk(-x[q][c].re, -x[q][c].im);
+            }
+            reconstruct<MU, true, R>(acc[r], x);
+        }
+    }
+    // backward: V(x - mu, mu)^+ (1 + g_mu) psi(x - mu)
+    {
+        int64_t sb = qs_nbr(g, s, MU, -1, &sg);
+        bool mb;
+        int64_t pb = qs_phys(g, sb, &mb);
+        load_link<R>(a.links, g.Vphys, MU, pb, U);
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) {
+            R v[24];
+            load24<R>(a.in + ((int64_t)r * g.Ns + sb) * 24, v);
+            C2<R> h[2][3], x[2][3];
+            project<MU, false, R>(v, h);
+            mul_link_dag<R>(U, mb, h, x);
+            if (MU == 0 && sg < 0) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) x[q][c] = cmk(-x[q][c].re, -x[q][c].im);
+            }
+            reconstruct<MU, false, R>(acc[r], x);
+        }
+    }
+}
+
+// element (i, j) of a packed Hermitian 6x6 block held in registers c[36]
+template <typename R>
+__device__ __forceinline__ C2<R> herm(const R c[36], int i, int j)
+{
+    if (i == j) return cmk(c[i], R(0));
+    if (i > j) { int k = 6 + 2 * qs_tri(i, j); return cmk(c[k], c[k + 1]); }
+    int k = 6 + 2 * qs_tri(j, i);
+    return cmk(c[k], -c[k + 1]);
+}
+
+template <typename R, int NRHS>
+__global__ void __launch_bounds__(128) dslash_kernel(DslashArgs<R> a)
+{
+    const Geom &g = a.g;
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= g.Ns) return;
+    bool mir;
+    int64_t p = qs_phys(g, s, &mir);
+
+    C2<R> hop[NRHS][12];
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r)
+#pragma unroll
+        for (int i = 0; i < 12; ++i) hop[r][i] = cmk(R(0), R(0));
+    hop_dir<0, R, NRHS>(a, s, p, mir, hop);
+    hop_dir<1, R, NRHS>(a, s, p, mir, hop);
+    hop_dir<2, R, NRHS>(a, s, p, mir, hop);
+    hop_dir<3, R, NRHS>(a, s, p, mir, hop);
+
+    // diagonal part and output, one chiral block (spins 2b, 2b+1) at a time.
+    // Mirror sites use A' = S conj(A) S, S = s_2 (x) 1, i.e.
+    // A'[i][j] = (same spin half ? 1 : -1) * conj(A[i +- 3][j +- 3]).
+    R out[NRHS][24];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        R c[36];
+#pragma unroll
+        for (int k = 0; k < 36; ++k) c[k] = __ldg(a.clov + (int64_t)(b * 36 + k) * g.Vphys + p);
+#pragma unroll
+        for (int r = 0; r < NRHS; ++r) {
+            R v[24];
+            load24<R>(a.in + ((int64_t)r * g.Ns + s) * 24, v);
+            R dm = R(4) + (R)a.m0[r];
+            R gsign = (a.gamma5 && b == 1) ? R(-1) : R(1);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                C2<R> acc = dm * cmk(v[(b * 6 + i) * 2], v[(b * 6 + i) * 2 + 1]);
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    C2<R> e;
+                    if (mir) {
+                        int is = (i + 3) % 6, js = (j + 3) % 6;
+                        e = conjc(herm<R>(c, is, js));
+                        if ((i < 3) != (j < 3)) e = cmk(-e.re, -e.im);
+                    } else {
+                        e = herm<R>(c, i, j);
+                    }
+                    acc = acc + e * cmk(v[(b * 6 + j) * 2], v[(b * 6 + j) * 2 + 1]);
+                }
+                C2<R> hv = hop[r][b * 6 + i];
+                out[r][(b * 6 + i) * 2] = gsign * (acc.re - R(0.5) * hv.re);
+                out[r][(b * 6 + i) * 2 + 1] = gsign * (acc.im - R(0.5) * hv.im);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NRHS; ++r) store24<R>(a.out + ((int64_t)r * g.Ns + s) * 24, out[r]);
+}
+
+template <typename R, int NRHS>
+cudaError_t launch_nrhs(const DslashArgs<R> &a, cudaStream_t st)
+{
+    int nb = (int)((a.g.Ns + 127) / 128);
+    dslash_kernel<R, NRHS><<<nb, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t qs_dslash_launch(DslashArgs<R> a, int nrhs, cudaStream_t st)
+{
+    // FP32 takes up to 4 right-hand sides per thread, FP64 up to 2 (registers)
+    const int maxr = sizeof(R) == 4 ? 4 : 2;
+    int done = 0;
+    while (done < nrhs) {
+        int n = nrhs - done;
+        if (n > maxr) n = maxr;
+        if (n == 3) n = 2;
+        DslashArgs<R> b = a;
+        b.in = a.in + (int64_t)done * a.g.Ns * 24;
+        b.out = a.out + (int64_t)done * a.g.Ns * 24;
+        for (int r = 0; r < n; ++r) b.m0[r] = a.m0[done + r];
+        cudaError_t e;
+        if (n == 4) e = launch_nrhs<R, 4>(b, st);
+        else if (n == 2) e = launch_nrhs<R, 2>(b, st);
+        else e = launch_nrhs<R, 1>(b, st);
+        if (e != cudaSuccess) return e;
+        done += n;
+    }
+    return cudaSuccess;
+}
+
+template cudaError_t qs_dslash_launch<double>(DslashArgs<double>, int, cudaStream_t);
+template cudaError_t qs_dslash_launch<float>(DslashArgs<float>, int, cudaStream_t);

@@ -1,0 +1,137 @@
+// Internal definitions of the qstar library (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+#include "../../include/qstar.h"
+
+// ---------------------------------------------------------------------------
+// error plumbing: no call aborts; CUDA errors become QS_ECUDA
+// ---------------------------------------------------------------------------
+void qs_record_cuda_error(cudaError_t e, const char *where);
+
+#define QS_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t _e = (call);                                             \
+        if (_e != cudaSuccess) {                                             \
+            qs_record_cuda_error(_e, #call);                                 \
+            return _e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA;   \
+        }                                                                    \
+    } while (0)
+
+#define QS_TRY(expr)                    \
+    do {                                \
+        int _s = (expr);                \
+        if (_s != QS_OK) return _s;     \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// geometry of the doubled lattice (T x L x L x 2L), see include/qstar.h
+// ---------------------------------------------------------------------------
+struct Geom {
+    int L, T, L2;          // L2 = 2L
+    int cstar_y, cstar_z;  // C* in y / z (x always)
+    int t_anti;
+    int64_t Ns, Vphys;     // doubled sites, physical sites
+    int64_t sy, sz, st;    // strides of y, z, t in the doubled site index
+};
+
+struct qs_lattice {
+    Geom g;
+    int device;
+    cudaStream_t stream;
+    int gauge_loaded;
+    double csw_su3, csw_u1;
+    // V = U exp(i theta) on the physical lattice, SoA [mu][9][Vphys] complex
+    double2 *links64;
+    float2 *links32;
+    // SW term A on the physical lattice: [72][Vphys] reals (two packed 6x6
+    // Hermitian blocks); the mirror site's blocks are derived on the fly
+    double *clov64;
+    float *clov32;
+};
+
+// neighbour of doubled site s in direction mu, step +1/-1; *sgn = fermion bc factor
+__host__ __device__ inline int64_t qs_nbr(const Geom &g, int64_t s, int mu, int step, int *sgn)
+{
+    int x = (int)(s % g.L2);
+    int64_t r = s / g.L2;
+    int y = (int)(r % g.L);
+    r /= g.L;
+    int z = (int)(r % g.L);
+    int t = (int)(r / g.L);
+    *sgn = 1;
+    switch (mu) {
+    case 0: {
+        int tn = t + step;
+        if (tn < 0 || tn >= g.T) {
+            tn = (tn + g.T) % g.T;
+            if (g.t_anti) *sgn = -1;
+        }
+        return s + (int64_t)(tn - t) * g.st;
+    }
+    case 1: {
+        int xn = (x + step + g.L2) % g.L2;
+        return s + (xn - x);
+    }
+    case 2: {
+        int yn = y + step;
+        int xn = x;
+        if (yn < 0 || yn >= g.L) {
+            yn = (yn + g.L) % g.L;
+            if (g.cstar_y) xn = (x + g.L) % g.L2;
+        }
+        return s + (int64_t)(yn - y) * g.sy + (xn - x);
+    }
+    default: {
+        int zn = z + step;
+        int xn = x;
+        if (zn < 0 || zn >= g.L) {
+            zn = (zn + g.L) % g.L;
+            if (g.cstar_z) xn = (x + g.L) % g.L2;
+        }
+        return s + (int64_t)(zn - z) * g.sz + (xn - x);
+    }
+    }
+}
+
+// physical site of doubled site s, and whether s is on the mirror (antiquark) half
+__host__ __device__ inline int64_t qs_phys(const Geom &g, int64_t s, bool *mirror)
+{
+    int x = (int)(s % g.L2);
+    *mirror = x >= g.L;
+    return (s / g.L2) * g.L + (x >= g.L ? x - g.L : x);
+}
+
+// ---------------------------------------------------------------------------
+// small complex helpers (R = float or double)
+// ---------------------------------------------------------------------------
+template <typename R> struct C2 { R re, im; };
+
+template <typename R> __host__ __device__ inline C2<R> cmk(R a, R b) { C2<R> c; c.re = a; c.im = b; return c; }
+template <typename R> __host__ __device__ inline C2<R> operator+(C2<R> a, C2<R> b) { return cmk(a.re + b.re, a.im + b.im); }
+template <typename R> __host__ __device__ inline C2<R> operator-(C2<R> a, C2<R> b) { return cmk(a.re - b.re, a.im - b.im); }
+template <typename R> __host__ __device__ inline C2<R> operator*(C2<R> a, C2<R> b)
+{
+    return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R> __host__ __device__ inline C2<R> operator*(R a, C2<R> b) { return cmk(a * b.re, a * b.im); }
+template <typename R> __host__ __device__ inline C2<R> conjc(C2<R> a) { return cmk(a.re, -a.im); }
+// multiply by i
+template <typename R> __host__ __device__ inline C2<R> mul_i(C2<R> a) { return cmk(-a.im, a.re); }
+// a * conj(b)
+template <typename R> __host__ __device__ inline C2<R> mul_cj(C2<R> a, C2<R> b)
+{
+    return cmk(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+// conj(a) * b
+template <typename R> __host__ __device__ inline C2<R> cj_mul(C2<R> a, C2<R> b)
+{
+    return cmk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+
+// packed Hermitian 6x6: 6 real diagonals then 15 complex strict-lower entries
+// (i > j) in row order; index of (i, j) is i (i - 1) / 2 + j
+__host__ __device__ inline int qs_tri(int i, int j) { return i * (i - 1) / 2 + j; }
+
+Geom qs_make_geom(int L, int T, int cstar_mask, int t_anti);

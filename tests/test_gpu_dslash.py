@@ -1,0 +1,140 @@
+"""Parity of the CUDA operator (apply_Dw / apply_Q through the C-ABI) with the oracle.
+
+Tolerances (relative, max-norm over all compared components): 1e-10 for FP64 and
+1e-5 for FP32 operator applications.
+"""
+import numpy as np
+import pytest
+
+from synth_inputs import WORKLOADS, GaugeConfig, kappa_to_m0, make_config, random_spinor
+from oracle.dirac import WilsonDirac
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-10, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import paper_2108_11989_gb300 as qs
+    return qs
+
+
+def _to_dev(psi, dt):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(psi).view(np.float64).copy()).to(dt).cuda()
+
+
+def _from_dev(t, shape):
+    return t.double().cpu().numpy().view(np.complex128).reshape(shape)
+
+
+def check(qs, cfg, m0, prec, nrhs, gamma5, sites=None, seed=3):
+    import torch
+    dt = torch.float64 if prec == "f64" else torch.float32
+    lat = qs.Lattice(cfg.L, cfg.T, cfg.cstar_mask, cfg.t_antiperiodic)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    psi = random_spinor(seed, cfg.T, cfg.L, nrhs)
+    if prec == "f32":
+        psi = psi.astype(np.complex64).astype(np.complex128)   # the oracle sees the same inputs
+    x = _to_dev(psi, dt)
+    y = torch.empty_like(x)
+    (lat.apply_Q if gamma5 else lat.apply_Dw)(m0, x, y)
+    torch.cuda.synchronize()
+    got = _from_dev(y, psi.shape).reshape(nrhs, -1, 12)
+    op = WilsonDirac(cfg, lazy=sites is not None)
+    fn = op.apply_Q if gamma5 else op.apply_D
+    worst = 0.0
+    for r in range(nrhs):
+        ref = fn(psi[r].reshape(-1), m0, sites)
+        ref = ref.reshape(-1, 12)
+        g = got[r] if sites is None else got[r][sites]
+        err = np.abs(g - ref).max() / np.abs(ref).max()
+        worst = max(worst, err)
+    lat.close()
+    assert worst <= TOL[prec], (prec, nrhs, gamma5, worst)
+    return worst
+
+
+def tiny_cfg():
+    return make_config(seed=0, **WORKLOADS["tiny_4x4x4x4"])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("gamma5", [False, True])
+def test_tiny_workload(qs, prec, gamma5):
+    check(qs, tiny_cfg(), kappa_to_m0(0.135), prec, 1, gamma5)
+
+
+@pytest.mark.parametrize("prec,nrhs", [("f64", 3), ("f32", 5), ("f32", 4), ("f64", 2)])
+def test_smallest_lattice_all_boundaries(qs, prec, nrhs):
+    # 2^3 x 3: every site touches every boundary; antiperiodic t, C* in x, y only
+    cfg = make_config(T=3, L=2, eps=0.8, theta_sigma=0.4, csw_su3=1.3, csw_u1=0.7, seed=9,
+                      t_antiperiodic=True, cstar_mask=0b011)
+    check(qs, cfg, -0.41, prec, nrhs, True)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ragged_tail(qs, prec):
+    # N_s = 2 * 6^3 * 5 = 2160: not a multiple of the 128-thread block; C* in x and z
+    cfg = make_config(T=5, L=6, eps=0.5, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=4,
+                      cstar_mask=0b101)
+    check(qs, cfg, 0.13, prec, 3, False)
+
+
+def test_free_field_plane_wave_gpu(qs):
+    """Closed form at a size the oracle is not needed for: free field, C* momentum."""
+    import torch
+    from oracle.gamma import GAMMA
+    T, L = 8, 8
+    su3 = np.zeros((T, L, L, L, 4, 3, 3), dtype=np.complex128)
+    su3[..., 0, 0] = su3[..., 1, 1] = su3[..., 2, 2] = 1
+    lat = qs.Lattice(L, T)
+    lat.load_gauge(su3, None, 1.9, 0.0)
+    t, z, y, x = np.meshgrid(np.arange(T), np.arange(L), np.arange(L), np.arange(2 * L), indexing="ij")
+    p1 = np.pi * 3 / L
+    p = (2 * np.pi * 1 / T, p1, p1 + 2 * np.pi * 2 / L, p1 + 2 * np.pi * 5 / L)
+    ph = np.exp(1j * (p[0] * t + p[1] * x + p[2] * y + p[3] * z))
+    u = np.random.default_rng(0).standard_normal((4, 3)) + 0j
+    psi = ph[..., None, None] * u
+    m0 = -0.2
+    Dp = (m0 + sum(1 - np.cos(q) for q in p)) * np.eye(4) + 1j * sum(GAMMA[m] * np.sin(p[m]) for m in range(4))
+    ref = ph[..., None, None] * (Dp @ u)
+    xx = _to_dev(psi, torch.float64)
+    yy = torch.empty_like(xx)
+    lat.apply_Dw(m0, xx, yy)
+    got = _from_dev(yy, psi.shape)
+    assert np.abs(got - ref).max() < 1e-12
+    lat.close()
+
+
+@pytest.fixture(scope="module")
+def cfg16():
+    return make_config(seed=0, **WORKLOADS["qcdqed_16x16x16x32"])
+
+
+@pytest.mark.parametrize("prec,nrhs", [("f64", 1), ("f32", 1), ("f32", 4), ("f64", 2)])
+def test_full_size_16x32_sampled(qs, cfg16, prec, nrhs):
+    """16^3 x 32 (N_s = 262144) at the benchmark's launch shapes; oracle on 1500 sampled sites."""
+    rng = np.random.default_rng(11)
+    ns = cfg16.n_sites
+    sites = np.unique(np.concatenate([rng.choice(ns, 1400, replace=False),
+                                      np.arange(64), np.arange(ns - 64, ns)]))
+    check(qs, cfg16, kappa_to_m0(0.135), prec, nrhs, True, sites=sites)
+
+
+def test_errors(qs):
+    import torch
+    cfg = tiny_cfg()
+    lat = qs.Lattice(cfg.L, cfg.T)
+    x = torch.zeros(cfg.n_sites * 24, dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    with pytest.raises(qs.QStarError) as e:     # gauge not loaded yet
+        lat.apply_Dw(0.1, x, y)
+    assert e.value.code == -1
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    with pytest.raises(qs.QStarError):          # in == out
+        lat.apply_Dw(0.1, x, x)
+    with pytest.raises(qs.QStarError):          # bad geometry: odd L
+        qs.Lattice(3, 4)
+    lat.close()

@@ -171,3 +171,15 @@ def test_clover_single_flux_plaquette(group):
     assert np.allclose(op.A[lat.index(t, z, y + 1, x + L)], -ref, atol=1e-14)
     # far away the clover term vanishes
     assert np.allclose(op.A[lat.index((t + 2) % T, z, y, x)], 0, atol=1e-14)
+
+
+def test_lazy_site_blocks_match_full_assembly():
+    cfg = rough_cfg(T=4, L=2, seed=8)
+    full, lazy = WilsonDirac(cfg), WilsonDirac(cfg, lazy=True)
+    rng = np.random.default_rng(0)
+    psi = rng.standard_normal(full.n) + 1j * rng.standard_normal(full.n)
+    sites = np.array([0, 5, 17, 63])
+    a = full.apply_Q(psi, -0.2).reshape(-1, 12)[sites]
+    b = lazy.apply_Q(psi, -0.2, sites)
+    assert np.allclose(a, b, atol=1e-14)
+    assert np.allclose(full.sparse_Q(-0.2) @ psi, full.apply_Q(psi, -0.2), atol=1e-13)
