@@ -1,0 +1,277 @@
+"""Benchmark of the Pfaffian-sign hot path on one GB300 (or N replicas).
+
+Workload: the synthetic 16^3 x 32 QCD+QED configuration (C* in x, y, z, periodic t,
+SU(3) links exp(i 0.2 H), U(1) angles N(0, 0.3^2), c_sw = 1.9 / 1.0), doubled to
+N_s = 262144 sites.  One step = Q = gamma_5 D applied in FP32 to a block of
+``--nrhs`` vectors (the operator application that dominates every inner solve of
+the sign computation).  Each step uses a different set of input/output buffers
+(4 sets, together far larger than the 129 MB L2), so no step reads what the
+previous one left in L2.
+
+value   = algorithmic operator bytes moved per second (GB/s): per doubled site and
+          right-hand side 24 + 24 spinor reals, plus per site 36 link reals and 36
+          SW-term reals shared by all right-hand sides of the launch (each physical
+          link and SW block serves the site and its mirror).
+e2e     = the same metric through the C-ABI with HOST buffers: every step copies
+          its input from pinned host memory and reads its result back.
+roofline: dominant kernel (the operator), achieved GB/s from CUDA events on the
+          launching stream, against the measured HBM copy bandwidth.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "qcdqed_16x16x16x32"
+METRIC = "Dslash GB/s (% HBM peak); Pf-sign time/config, mixed+batched vs plain FP64 GPU"
+KAPPA = 0.135
+
+
+def reals_per_site(nrhs):
+    return 48 * nrhs + 72
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d["hbm_gbs"], "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = sorted(float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit())
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    import torch
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(cfg, m0, seconds=12.0):
+    """The oracle's apply_Q (FP64, numpy) on sampled output sites of the same lattice."""
+    import numpy as np
+    from oracle.dirac import WilsonDirac
+    from synth_inputs import random_spinor
+    op = WilsonDirac(cfg, lazy=True)
+    psi = random_spinor(1, cfg.T, cfg.L).reshape(-1)
+    rng = np.random.default_rng(0)
+    chunk = 2048
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        sites = rng.choice(cfg.n_sites, chunk, replace=False)
+        op.apply_Q(psi, m0, sites)
+        done += chunk
+    dt = time.perf_counter() - t0
+    gbs = done * reals_per_site(1) * 8 / dt / 1e9
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} output sites of the {cfg.L}^3x{cfg.T} lattice in chunks of {chunk}, "
+                      f"FP64 numpy, {dt:.1f} s; bytes counted with the same per-site model (nrhs=1, FP64)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return
+    from synth_inputs import WORKLOADS, kappa_to_m0, make_config
+    cfg = make_config(seed=0, **WORKLOADS[WORKLOAD])
+    m0 = kappa_to_m0(KAPPA)
+    vals = []
+    per_step = max(0.3, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(cfg, m0, seconds=per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(cfg, m0, seconds=per_step))
+    total = time.perf_counter() - t0
+    v = sum(x["value"] for x in vals) / len(vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s",
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": WORKLOAD, "nrhs": 1, "prec": "f64",
+                                 "l2": "oracle on host cores"},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    import paper_2108_11989_gb300 as qs
+    from synth_inputs import WORKLOADS, kappa_to_m0, make_config, random_spinor
+
+    cfg = make_config(seed=rank, **WORKLOADS[WORKLOAD])
+    m0 = kappa_to_m0(KAPPA)
+    stream = torch.cuda.current_stream()
+    lat = qs.Lattice(cfg.L, cfg.T, device=local, stream=stream)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    ns, R = cfg.n_sites, args.nrhs
+    nsets = 4
+    rdt = np.float32 if args.prec == "f32" else np.float64
+    rsz = 4 if args.prec == "f32" else 8
+    bufs = []
+    for k in range(nsets):
+        psi = random_spinor(100 + k, cfg.T, cfg.L, R)
+        x = torch.from_numpy(psi.view(np.float64).astype(rdt)).cuda().reshape(-1)
+        bufs.append((x, torch.empty_like(x)))
+    bytes_per_launch = ns * reals_per_site(R) * rsz
+    per = 4 if args.prec == "f32" else 2
+    launches_per_step = 0
+    left = R
+    while left > 0:
+        n = min(left, per)
+        n = 2 if n == 3 else n
+        left -= n
+        launches_per_step += 1
+
+    def step(k):
+        x, y = bufs[k % nsets]
+        lat.apply_Q(m0, x, y)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step(k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(ws)
+    clk = clocks.stop()
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    total_ms = max_over_ranks(total_ms, ws)
+    ms_step = total_ms / args.steps
+    value = ws * bytes_per_launch * args.steps / (total_ms * 1e-3) / 1e9
+    avg_step_s = sum(kern_ms) / len(kern_ms) * 1e-3
+    achieved = bytes_per_launch / avg_step_s / 1e9
+    peak, src = peaks()
+
+    # end to end through the C-ABI with host buffers
+    hx = torch.empty(bufs[0][0].numel(), dtype=bufs[0][0].dtype, pin_memory=True)
+    hx.copy_(bufs[0][0].cpu())
+    hy = torch.empty_like(hx, pin_memory=True)
+    dx, dy = torch.empty_like(bufs[0][0]), torch.empty_like(bufs[0][0])
+    e_steps = max(10, args.steps // 4)
+    for _ in range(3):
+        dx.copy_(hx, non_blocking=True); lat.apply_Q(m0, dx, dy); hy.copy_(dy, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        dx.copy_(hx, non_blocking=True)
+        lat.apply_Q(m0, dx, dy)
+        hy.copy_(dy, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks(e0.elapsed_time(e1), ws)
+    e2e = ws * bytes_per_launch * e_steps / (e_ms * 1e-3) / 1e9
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": f"{cfg.L}^3x{cfg.T} (doubled N_s={ns})",
+                   "op": "Q = gamma5 D", "prec": args.prec, "nrhs": R, "m0": m0,
+                   "l2": f"inputs larger than L2: {nsets} buffer sets rotated",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{src} hbm_gbs", "bytes_model": f"{reals_per_site(R)} reals/site x {rsz} B"},
+        "e2e": {"value": e2e, "unit": "GB/s", "h2d_bytes_per_step": hx.numel() * rsz,
+                "d2h_bytes_per_step": hy.numel() * rsz},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, m0)
+    if rank == 0:
+        print(json.dumps(out))
+    lat.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
