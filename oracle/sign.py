@@ -21,7 +21,8 @@ Three routes, all FP64 on the CPU:
    of eigenvalues in (-a, 0).  By |lambda'| <= 1 (eq. derivativebound) no eigenvalue
    outside (-a, a) can change sign in the step, and the eigenvalues inside stay
    inside, so the change of N_- is exact.  Return to step A as soon as lambda_bar
-   grows again.
+   grows again.  Step 4 also fires when m + (lambda_bar - r) > m0_max: the interval
+   (m - lambda_bar, m + lambda_bar) of eq. derivativebound already covers m0_max.
 
 Pinned by tests/test_oracle_sign.py: routes 1 and 2 agree (the theorem of
 Sec. 3), sign +1 above m0_max, and the flow agrees with both on tiny lattices,
@@ -107,7 +108,7 @@ def pfaffian_sign_flow(modes_fn, m_target, m0_max, c=1.9, max_steps=200, min_ste
                     if not covered:                   # restart B from the last covered mass
                         m, cur = pm, pcur
                     break
-            if m > m0_max:                           # step 4
+            if m > m0_max or m + (lb - rb) > m0_max:   # step 4 (or its interval covers m0_max)
                 return (1 if flips % 2 == 0 else -1), report
             pm, pcur, prev = m, cur, (lb, rb)
             m = m + c * lb                           # step 5
