@@ -94,6 +94,96 @@ QS_API int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, in
 /* out = Q(m0) in = gamma_5 D(m0) in (Sec. 3).  Same arguments as qs_apply_Dw. */
 QS_API int qs_apply_Q(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec);
 
+/* ---------------------------------------------------------------------------
+ * Low modes of Q(m0) (Sec. 3: lambda_bar = min_n |lambda_n| "by the power method
+ * plus Chebyshev acceleration"; the eigenvalues closest to zero are what the
+ * sign algorithm follows across masses).
+ *
+ * Method: block subspace iteration with Rayleigh-Ritz of Q in FP64.  While the
+ * relative residuals are large, each pass applies a Chebyshev filter in Q^2 (FP32
+ * storage and arithmetic) that damps the interval [theta_k^2, lambda_max^2];
+ * near convergence, passes are power steps with Q^-2, each solve a CG on Q^2 with
+ * FP32 inner iterations and FP64 defect correction.  Every eigenvalue returned is
+ * a Ritz value of the FP64 Q with its residual r = ||Q v - theta v||, so some
+ * eigenvalue of Q lies in [theta - r, theta + r].
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int k;             /* block size = eigenpairs returned, even, 2..64 */
+    int nwant;         /* the nwant smallest |theta| must meet tol (1..k) */
+    double tol;        /* target: r_i <= tol * |theta_i| for i < nwant */
+    int max_iter;      /* cap on subspace passes (filter + refinement) */
+    int cheb_degree;   /* degree of the Q^2 Chebyshev filter (>= 2) */
+    int warm_start;    /* 1: start from the subspace the handle kept from its last call */
+    uint64_t seed;     /* seed of the random start block */
+} qs_eig_opts;
+
+typedef struct {
+    int iterations;          /* subspace passes done */
+    int filter_passes, refine_passes;
+    int64_t dslash_f32, dslash_f64;   /* single-vector operator applications */
+    int64_t cg_iterations;   /* inner FP32 CG iterations (per block) */
+    double seconds;          /* wall time of the call */
+} qs_eig_stats;
+
+/* Fill *opts with defaults (k = 16, nwant = 4, tol = 1e-8, max_iter = 200,
+ * cheb_degree = 24, warm_start = 1, seed = 1). */
+QS_API void qs_eig_default_opts(qs_eig_opts *opts);
+
+/* Lowest-|lambda| eigenpairs of Q(m0) on the handle's gauge field.
+ * evals, resid: HOST arrays of k doubles, sorted by increasing |theta| (signed
+ *   Ritz values and residual norms ||Q v - theta v||).
+ * evecs: NULL, or a DEVICE buffer of k * N_s * 24 doubles (canonical layout) that
+ *   receives the orthonormal Ritz vectors.
+ * stats: NULL or receives counters.  Returns QS_ENOCONV (with the best values so
+ * far written) if max_iter passes do not reach tol.  Synchronises the stream. */
+QS_API int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts *opts, double *evals,
+                               double *resid, void *evecs, qs_eig_stats *stats);
+
+/* ---------------------------------------------------------------------------
+ * Sign of the Pfaffian (Sec. 3, eq. power1/4 and the enumerated algorithm).
+ * W_sgn(m0) = (-1)^(number of zero crossings of eigenvalues of Q between m0 and
+ * large mass), counted along the mass flow:
+ *  step A (Sec. 3, steps 1-5): m <- m + c lambda_bar while lambda_bar does not
+ *    decrease; stop with the sign found so far once m > m0_max.  Each step is
+ *    certified by |lambda'| <= 1 (eq. derivativebound) with lower bounds
+ *    lambda_bar - r: (lb_n - r_n) + (lb_{n+1} - r_{n+1}) >= m_{n+1} - m_n.
+ *  step B (the paper defers it to other work; our reading): from the last
+ *    certified mass, step by dm inside a spectral gap (a - dm, a + dm) of the
+ *    tracked window and add the change of the number of eigenvalues in (-a, 0);
+ *    return to step A when lambda_bar grows again.
+ * ------------------------------------------------------------------------- */
+#define QS_TRACE_MAX 1024
+
+typedef struct {
+    double c;          /* step factor of step A, slightly below 2 */
+    double m0_max;     /* step A stops above it; <= 0 selects 3 (c_sw + c_sw,U(1)) */
+    int max_steps;     /* cap on masses visited */
+    qs_eig_opts eig;   /* low-mode solver options (warm starts between masses) */
+} qs_sign_opts;
+
+typedef struct {
+    int n;                              /* masses visited */
+    double mass[QS_TRACE_MAX];
+    double lambda_bar[QS_TRACE_MAX];    /* min |theta| at that mass */
+    double resid[QS_TRACE_MAX];         /* residual bound of that theta */
+    char phase[QS_TRACE_MAX];           /* 'A' or 'B' */
+    int crossings;                      /* zero crossings counted by step B */
+    int steps_a, steps_b;
+    int64_t dslash_f32, dslash_f64;
+    int64_t cg_iterations;
+    double seconds;
+} qs_sign_report;
+
+/* Fill *opts with defaults (c = 1.9, m0_max = 0 (auto), max_steps = 400, eig defaults
+ * with tol = 1e-5).  Step A also stops as soon as m + (lambda_bar - r) > m0_max. */
+QS_API void qs_sign_default_opts(qs_sign_opts *opts);
+
+/* *sign = W_sgn(m0_target) in {+1, -1}.  report may be NULL.  Returns
+ * QS_EUNDECIDED if lambda_bar at the target is not certified > 0, QS_ENOCONV if
+ * the flow exceeds max_steps or an eigensolve does not converge. */
+QS_API int qs_pfaffian_sign(qs_lattice *lat, double m0_target, const qs_sign_opts *opts, int *sign,
+                            qs_sign_report *report);
+
 /* Static description of a status code. */
 QS_API const char *qs_strerror(int status);
 

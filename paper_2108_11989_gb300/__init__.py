@@ -13,6 +13,7 @@ import numpy as np
 from .build import LIB
 
 __all__ = ["QStarError", "Lattice", "create_lattice", "load_gauge", "apply_Dw", "apply_Q",
+           "lowmodes_at_mass", "pfaffian_sign", "eig_default_opts", "sign_default_opts",
            "strerror", "QS_F64", "QS_F32", "lib"]
 
 QS_F64, QS_F32 = 0, 1
@@ -31,6 +32,43 @@ class _Geom(ctypes.Structure):
                 ("t_antiperiodic", ctypes.c_int), ("device", ctypes.c_int)]
 
 
+class EigOpts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("nwant", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class EigStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("filter_passes", ctypes.c_int), ("refine_passes", ctypes.c_int),
+                ("dslash_f32", ctypes.c_int64), ("dslash_f64", ctypes.c_int64),
+                ("cg_iterations", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+
+QS_TRACE_MAX = 1024
+
+
+class SignOpts(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("m0_max", ctypes.c_double), ("max_steps", ctypes.c_int),
+                ("eig", EigOpts)]
+
+
+class SignReport(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("mass", ctypes.c_double * QS_TRACE_MAX),
+                ("lambda_bar", ctypes.c_double * QS_TRACE_MAX), ("resid", ctypes.c_double * QS_TRACE_MAX),
+                ("phase", ctypes.c_char * QS_TRACE_MAX), ("crossings", ctypes.c_int),
+                ("steps_a", ctypes.c_int), ("steps_b", ctypes.c_int),
+                ("dslash_f32", ctypes.c_int64), ("dslash_f64", ctypes.c_int64),
+                ("cg_iterations", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        n = min(self.n, QS_TRACE_MAX)
+        return {"n": self.n, "mass": list(self.mass[:n]), "lambda_bar": list(self.lambda_bar[:n]),
+                "resid": list(self.resid[:n]), "phase": self.phase[:n].decode(),
+                "crossings": self.crossings, "steps_a": self.steps_a, "steps_b": self.steps_b,
+                "dslash_f32": self.dslash_f32, "dslash_f64": self.dslash_f64,
+                "cg_iterations": self.cg_iterations, "seconds": self.seconds}
+
+
 def _load():
     if not os.path.exists(LIB):
         raise ImportError(f"libqstar.so is not built ({LIB}); run __graft_entry__.build() "
@@ -44,6 +82,11 @@ def _load():
         "qs_load_gauge": (I, [P, P, P, D, D]),
         "qs_apply_Dw": (I, [P, D, P, P, I, I]),
         "qs_apply_Q": (I, [P, D, P, P, I, I]),
+        "qs_eig_default_opts": (None, [ctypes.POINTER(EigOpts)]),
+        "qs_lowmodes_at_mass": (I, [P, D, ctypes.POINTER(EigOpts), P, P, P, ctypes.POINTER(EigStats)]),
+        "qs_sign_default_opts": (None, [ctypes.POINTER(SignOpts)]),
+        "qs_pfaffian_sign": (I, [P, D, ctypes.POINTER(SignOpts), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(SignReport)]),
         "qs_strerror": (ctypes.c_char_p, [I]),
         "qs_last_cuda_error": (ctypes.c_char_p, []),
     }
@@ -116,6 +159,50 @@ def apply_Q(h, m0, inp, out):
                            _prec_of(inp)), "apply_Q")
 
 
+def eig_default_opts(**kw):
+    o = EigOpts()
+    _lib.qs_eig_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def sign_default_opts(eig=None, **kw):
+    o = SignOpts()
+    _lib.qs_sign_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    if eig is not None:
+        for k, v in (eig.items() if isinstance(eig, dict) else []):
+            setattr(o.eig, k, v)
+    return o
+
+
+def lowmodes_at_mass(h, m0, opts=None, evecs=None, allow_noconv=False):
+    """qs_lowmodes_at_mass: returns (evals, resid, stats dict); evecs: optional device tensor."""
+    o = opts if opts is not None else eig_default_opts()
+    ev = np.zeros(o.k)
+    rs = np.zeros(o.k)
+    st = EigStats()
+    code = _lib.qs_lowmodes_at_mass(h, float(m0), ctypes.byref(o), ev.ctypes.data, rs.ctypes.data,
+                                    None if evecs is None else evecs.data_ptr(), ctypes.byref(st))
+    if not (code == 0 or (allow_noconv and code == -4)):
+        _check(code, "lowmodes_at_mass")
+    stats = {f: getattr(st, f) for f, _ in EigStats._fields_}
+    stats["status"] = code
+    return ev, rs, stats
+
+
+def pfaffian_sign(h, m0_target, opts=None):
+    """qs_pfaffian_sign: returns (sign, report dict)."""
+    o = opts if opts is not None else sign_default_opts()
+    sg = ctypes.c_int(0)
+    rep = SignReport()
+    _check(_lib.qs_pfaffian_sign(h, float(m0_target), ctypes.byref(o), ctypes.byref(sg), ctypes.byref(rep)),
+           "pfaffian_sign")
+    return sg.value, rep.as_dict()
+
+
 class Lattice:
     """Owning wrapper around a qs_lattice handle."""
 
@@ -132,6 +219,12 @@ class Lattice:
 
     def apply_Q(self, m0, inp, out):
         apply_Q(self.h, m0, inp, out)
+
+    def lowmodes_at_mass(self, m0, opts=None, evecs=None, allow_noconv=False):
+        return lowmodes_at_mass(self.h, m0, opts, evecs, allow_noconv)
+
+    def pfaffian_sign(self, m0_target, opts=None):
+        return pfaffian_sign(self.h, m0_target, opts)
 
     def close(self):
         if self.h is not None:

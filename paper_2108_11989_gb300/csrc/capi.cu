@@ -64,38 +64,90 @@ extern "C" int qs_destroy_lattice(qs_lattice *lat)
 
 extern "C" int64_t qs_n_sites(const qs_lattice *lat) { return lat ? lat->g.Ns : 0; }
 
-int qs_apply_op(qs_lattice *lat, const double *m0, const void *in, void *out, int nrhs, int prec,
-                int gamma5)
+template <typename R>
+static DslashArgs<R> make_args(qs_lattice *lat, const double *m0, const void *in, void *out, int nrhs,
+                               int gamma5);
+template <>
+DslashArgs<double> make_args<double>(qs_lattice *lat, const double *m0, const void *in, void *out,
+                                     int nrhs, int gamma5)
 {
-    if (!lat || !in || !out || nrhs < 1 || nrhs > QS_MAX_RHS) return QS_EINVAL;
-    if (!lat->gauge_loaded) return QS_EINVAL;
-    if (in == out) return QS_EINVAL;
-    size_t bytes = (size_t)nrhs * lat->g.Ns * 24 * (prec == QS_F64 ? 8 : 4);
-    const char *a = (const char *)in, *b = (const char *)out;
-    if (a < b + bytes && b < a + bytes) return QS_EINVAL;      // overlap
-    if (((uintptr_t)in | (uintptr_t)out) & 15) return QS_EINVAL; // vector loads need 16 B
-    QS_CUDA(cudaSetDevice(lat->device));
-    cudaError_t e;
-    if (prec == QS_F64) {
-        DslashArgs<double> d;
-        d.g = lat->g; d.links = lat->links64; d.clov = lat->clov64;
-        d.in = (const double *)in; d.out = (double *)out; d.gamma5 = gamma5;
-        for (int r = 0; r < nrhs; ++r) d.m0[r] = m0[r];
-        e = qs_dslash_launch<double>(d, nrhs, lat->stream);
-    } else if (prec == QS_F32) {
-        DslashArgs<float> d;
-        d.g = lat->g; d.links = lat->links32; d.clov = lat->clov32;
-        d.in = (const float *)in; d.out = (float *)out; d.gamma5 = gamma5;
-        for (int r = 0; r < nrhs; ++r) d.m0[r] = m0[r];
-        e = qs_dslash_launch<float>(d, nrhs, lat->stream);
-    } else {
-        return QS_EINVAL;
+    DslashArgs<double> d;
+    d.g = lat->g; d.links = lat->links64; d.clov = lat->clov64;
+    d.in = (const double *)in; d.out = (double *)out; d.gamma5 = gamma5; d.nrhs = nrhs;
+    for (int r = 0; r < nrhs; ++r) d.m0[r] = m0[r];
+    return d;
+}
+template <>
+DslashArgs<float> make_args<float>(qs_lattice *lat, const double *m0, const void *in, void *out,
+                                   int nrhs, int gamma5)
+{
+    DslashArgs<float> d;
+    d.g = lat->g; d.links = lat->links32; d.clov = lat->clov32;
+    d.in = (const float *)in; d.out = (float *)out; d.gamma5 = gamma5; d.nrhs = nrhs;
+    for (int r = 0; r < nrhs; ++r) d.m0[r] = m0[r];
+    return d;
+}
+
+template <typename R>
+static int run_typed(qs_lattice *lat, int pi, const double *m0, const void *in, void *out, int nrhs,
+                     int gamma5)
+{
+    DslashArgs<R> d = make_args<R>(lat, m0, in, out, nrhs, gamma5);
+    int &tv = lat->tuned[pi][nrhs];
+    if (tv == 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        QS_CUDA(cudaStreamIsCapturing(lat->stream, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            tv = 1 + (qs_dslash_nvariants<R>() > 2 ? 2 : 0);   // cannot time inside a capture
+        } else {
+            cudaEvent_t e0, e1;
+            QS_CUDA(cudaEventCreate(&e0));
+            QS_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            int bv = 0;
+            for (int v = 0; v < qs_dslash_nvariants<R>(); ++v) {
+                QS_CUDA(qs_dslash_launch<R>(d, nrhs, v, lat->stream));   // warm-up
+                QS_CUDA(cudaEventRecord(e0, lat->stream));
+                for (int rep = 0; rep < 3; ++rep) QS_CUDA(qs_dslash_launch<R>(d, nrhs, v, lat->stream));
+                QS_CUDA(cudaEventRecord(e1, lat->stream));
+                QS_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                QS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) { best = ms; bv = v; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            tv = bv + 1;
+        }
     }
+    cudaError_t e = qs_dslash_launch<R>(d, nrhs, tv - 1, lat->stream);
     if (e != cudaSuccess) {
         qs_record_cuda_error(e, "dslash launch");
         return QS_ECUDA;
     }
     return QS_OK;
+}
+
+int qs_dslash_run(qs_lattice *lat, int prec, const double *m0, const void *in, void *out, int nrhs,
+                  int gamma5)
+{
+    if (prec == QS_F64) return run_typed<double>(lat, 0, m0, in, out, nrhs, gamma5);
+    if (prec == QS_F32) return run_typed<float>(lat, 1, m0, in, out, nrhs, gamma5);
+    return QS_EINVAL;
+}
+
+int qs_apply_op(qs_lattice *lat, const double *m0, const void *in, void *out, int nrhs, int prec,
+                int gamma5)
+{
+    if (!lat || !in || !out || nrhs < 1 || nrhs > QS_MAX_RHS) return QS_EINVAL;
+    if (!lat->gauge_loaded) return QS_EINVAL;
+    if (prec != QS_F64 && prec != QS_F32) return QS_EINVAL;
+    size_t bytes = (size_t)nrhs * lat->g.Ns * 24 * (prec == QS_F64 ? 8 : 4);
+    const char *a = (const char *)in, *b = (const char *)out;
+    if (a < b + bytes && b < a + bytes) return QS_EINVAL;      // overlap
+    if (((uintptr_t)in | (uintptr_t)out) & 15) return QS_EINVAL; // vector loads need 16 B
+    QS_CUDA(cudaSetDevice(lat->device));
+    return qs_dslash_run(lat, prec, m0, in, out, nrhs, gamma5);
 }
 
 extern "C" int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec)
@@ -130,6 +182,3 @@ extern "C" const char *qs_strerror(int status)
 }
 
 extern "C" const char *qs_last_cuda_error(void) { return g_last_cuda_error; }
-
-// workspace of the solvers (none yet)
-void qs_free_workspace(qs_lattice *lat) { (void)lat; }

@@ -156,9 +156,9 @@ __device__ __forceinline__ void mul_link_dag(const C2<R> U[9], bool cj, const C2
         }
 }
 
-template <int MU, typename R, int NRHS>
-__device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, int64_t s, int64_t p, bool mir,
-                                        C2<R> acc[NRHS][12])
+template <int MU, typename R>
+__device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restrict__ in, int64_t s,
+                                        int64_t p, bool mir, C2<R> acc[12])
 {
     const Geom &g = a.g;
     C2<R> U[9];
@@ -166,149 +166,154 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, int64_t s, int64
     // forward: V(x, mu) (1 - g_mu) psi(x + mu)
     {
         int64_t sf = qs_nbr(g, s, MU, +1, &sg);
+        R v[24];
+        load24<R>(in + sf * 24, v);
         load_link<R>(a.links, g.Vphys, MU, p, U);
+        C2<R> h[2][3], x[2][3];
+        project<MU, true, R>(v, h);
+        mul_link<R>(U, mir, h, x);
+        if (MU == 0 && sg < 0) {
 #pragma unroll
-        for (int r = 0; r < NRHS; ++r) {
-            R v[24];
-            load24<R>(a.in + ((int64_t)r * g.Ns + sf) * 24, v);
-            C2<R> h[2][3], x[2][3];
-            project<MU, true, R>(v, h);
-            mul_link<R>(U, mir, h, x);
-            if (MU == 0 && sg < 0) {
+            for (int q = 0; q < 2; ++q)
 #pragma unroll
-                for (int q = 0; q < 2; ++q)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) x[q][c] = cmk(-x[q][c].re, -x[q][c].im);
-            }
-            reconstruct<MU, true, R>(acc[r], x);
+                for (int c = 0; c < 3; ++c) x[q][c] = cmk(-x[q][c].re, -x[q][c].im);
         }
+        reconstruct<MU, true, R>(acc, x);
     }
     // backward: V(x - mu, mu)^+ (1 + g_mu) psi(x - mu)
     {
         int64_t sb = qs_nbr(g, s, MU, -1, &sg);
         bool mb;
         int64_t pb = qs_phys(g, sb, &mb);
+        R v[24];
+        load24<R>(in + sb * 24, v);
         load_link<R>(a.links, g.Vphys, MU, pb, U);
+        C2<R> h[2][3], x[2][3];
+        project<MU, false, R>(v, h);
+        mul_link_dag<R>(U, mb, h, x);
+        if (MU == 0 && sg < 0) {
 #pragma unroll
-        for (int r = 0; r < NRHS; ++r) {
-            R v[24];
-            load24<R>(a.in + ((int64_t)r * g.Ns + sb) * 24, v);
-            C2<R> h[2][3], x[2][3];
-            project<MU, false, R>(v, h);
-            mul_link_dag<R>(U, mb, h, x);
-            if (MU == 0 && sg < 0) {
+            for (int q = 0; q < 2; ++q)
 #pragma unroll
-                for (int q = 0; q < 2; ++q)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) x[q][c] = cmk(-x[q][c].re, -x[q][c].im);
-            }
-            reconstruct<MU, false, R>(acc[r], x);
+                for (int c = 0; c < 3; ++c) x[q][c] = cmk(-x[q][c].re, -x[q][c].im);
         }
+        reconstruct<MU, false, R>(acc, x);
     }
 }
 
-// element (i, j) of a packed Hermitian 6x6 block held in registers c[36]
-template <typename R>
-__device__ __forceinline__ C2<R> herm(const R c[36], int i, int j)
-{
-    if (i == j) return cmk(c[i], R(0));
-    if (i > j) { int k = 6 + 2 * qs_tri(i, j); return cmk(c[k], c[k + 1]); }
-    int k = 6 + 2 * qs_tri(j, i);
-    return cmk(c[k], -c[k + 1]);
-}
-
-template <typename R, int NRHS>
-__global__ void __launch_bounds__(128) dslash_kernel(DslashArgs<R> a)
+// One thread per (doubled site, right-hand side); the right-hand side index runs
+// fastest, so the threads of one site sit next to each other and share the link
+// and SW-term loads through L1.
+template <typename R, int MINB>
+__global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
 {
     const Geom &g = a.g;
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t s = tid / a.nrhs;
+    int r = (int)(tid - s * a.nrhs);
     if (s >= g.Ns) return;
+    const R *in = a.in + (int64_t)r * g.Ns * 24;
     bool mir;
     int64_t p = qs_phys(g, s, &mir);
 
-    C2<R> hop[NRHS][12];
+    C2<R> acc[12];
 #pragma unroll
-    for (int r = 0; r < NRHS; ++r)
+    for (int i = 0; i < 12; ++i) acc[i] = cmk(R(0), R(0));
+    hop_dir<0, R>(a, in, s, p, mir, acc);
+    hop_dir<1, R>(a, in, s, p, mir, acc);
+    hop_dir<2, R>(a, in, s, p, mir, acc);
+    hop_dir<3, R>(a, in, s, p, mir, acc);
 #pragma unroll
-        for (int i = 0; i < 12; ++i) hop[r][i] = cmk(R(0), R(0));
-    hop_dir<0, R, NRHS>(a, s, p, mir, hop);
-    hop_dir<1, R, NRHS>(a, s, p, mir, hop);
-    hop_dir<2, R, NRHS>(a, s, p, mir, hop);
-    hop_dir<3, R, NRHS>(a, s, p, mir, hop);
+    for (int i = 0; i < 12; ++i) acc[i] = R(-0.5) * acc[i];
 
-    // diagonal part and output, one chiral block (spins 2b, 2b+1) at a time.
+    // diagonal part (4 + m0 + A), one chiral block (spins 2b, 2b+1) at a time.
     // Mirror sites use A' = S conj(A) S, S = s_2 (x) 1, i.e.
     // A'[i][j] = (same spin half ? 1 : -1) * conj(A[i +- 3][j +- 3]).
-    R out[NRHS][24];
+    R v[24];
+    load24<R>(in + s * 24, v);
+    const R dm = R(4) + (R)a.m0[r];
+    const R *cl = a.clov + p;
+    const int64_t V = g.Vphys;
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-        R c[36];
+        const R *cb = cl + (int64_t)b * 36 * V;
 #pragma unroll
-        for (int k = 0; k < 36; ++k) c[k] = __ldg(a.clov + (int64_t)(b * 36 + k) * g.Vphys + p);
+        for (int i = 0; i < 6; ++i) {
+            C2<R> t = dm * cmk(v[(b * 6 + i) * 2], v[(b * 6 + i) * 2 + 1]);
 #pragma unroll
-        for (int r = 0; r < NRHS; ++r) {
-            R v[24];
-            load24<R>(a.in + ((int64_t)r * g.Ns + s) * 24, v);
-            R dm = R(4) + (R)a.m0[r];
-            R gsign = (a.gamma5 && b == 1) ? R(-1) : R(1);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                C2<R> acc = dm * cmk(v[(b * 6 + i) * 2], v[(b * 6 + i) * 2 + 1]);
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    C2<R> e;
-                    if (mir) {
-                        int is = (i + 3) % 6, js = (j + 3) % 6;
-                        e = conjc(herm<R>(c, is, js));
-                        if ((i < 3) != (j < 3)) e = cmk(-e.re, -e.im);
-                    } else {
-                        e = herm<R>(c, i, j);
-                    }
-                    acc = acc + e * cmk(v[(b * 6 + j) * 2], v[(b * 6 + j) * 2 + 1]);
+            for (int j = 0; j < 6; ++j) {
+                // element (ii, jj) of the stored block; mirror sites read the
+                // spin-swapped element and conjugate it (A' = S conj(A) S)
+                const int ii = mir ? (i + 3) % 6 : i, jj = mir ? (j + 3) % 6 : j;
+                C2<R> e;
+                if (ii == jj) {
+                    e = cmk(__ldg(cb + ii * V), R(0));
+                } else if (ii > jj) {
+                    const int k = 6 + 2 * qs_tri(ii, jj);
+                    e = cmk(__ldg(cb + k * V), __ldg(cb + (k + 1) * V));
+                } else {
+                    const int k = 6 + 2 * qs_tri(jj, ii);
+                    e = cmk(__ldg(cb + k * V), -__ldg(cb + (k + 1) * V));
                 }
-                C2<R> hv = hop[r][b * 6 + i];
-                out[r][(b * 6 + i) * 2] = gsign * (acc.re - R(0.5) * hv.re);
-                out[r][(b * 6 + i) * 2 + 1] = gsign * (acc.im - R(0.5) * hv.im);
+                if (mir) {
+                    e = conjc(e);
+                    if ((i < 3) != (j < 3)) e = cmk(-e.re, -e.im);
+                }
+                t = t + e * cmk(v[(b * 6 + j) * 2], v[(b * 6 + j) * 2 + 1]);
             }
+            acc[b * 6 + i] = acc[b * 6 + i] + t;
         }
     }
+    R o[24];
+    const R gs = a.gamma5 ? R(-1) : R(1);
 #pragma unroll
-    for (int r = 0; r < NRHS; ++r) store24<R>(a.out + ((int64_t)r * g.Ns + s) * 24, out[r]);
-}
-
-template <typename R, int NRHS>
-cudaError_t launch_nrhs(const DslashArgs<R> &a, cudaStream_t st)
-{
-    int nb = (int)((a.g.Ns + 127) / 128);
-    dslash_kernel<R, NRHS><<<nb, 128, 0, st>>>(a);
-    return cudaGetLastError();
+    for (int i = 0; i < 12; ++i) {
+        R f = i >= 6 ? gs : R(1);
+        o[2 * i] = f * acc[i].re;
+        o[2 * i + 1] = f * acc[i].im;
+    }
+    store24<R>(a.out + ((int64_t)r * g.Ns + s) * 24, o);
 }
 
 }  // namespace
 
-template <typename R>
-cudaError_t qs_dslash_launch(DslashArgs<R> a, int nrhs, cudaStream_t st)
+template <typename R, int MINB>
+static cudaError_t launch_variant(const DslashArgs<R> &a, cudaStream_t st)
 {
-    // FP32 takes up to 4 right-hand sides per thread, FP64 up to 2 (registers)
-    const int maxr = sizeof(R) == 4 ? 4 : 2;
-    int done = 0;
-    while (done < nrhs) {
-        int n = nrhs - done;
-        if (n > maxr) n = maxr;
-        if (n == 3) n = 2;
-        DslashArgs<R> b = a;
-        b.in = a.in + (int64_t)done * a.g.Ns * 24;
-        b.out = a.out + (int64_t)done * a.g.Ns * 24;
-        for (int r = 0; r < n; ++r) b.m0[r] = a.m0[done + r];
-        cudaError_t e;
-        if (n == 4) e = launch_nrhs<R, 4>(b, st);
-        else if (n == 2) e = launch_nrhs<R, 2>(b, st);
-        else e = launch_nrhs<R, 1>(b, st);
-        if (e != cudaSuccess) return e;
-        done += n;
-    }
-    return cudaSuccess;
+    int64_t nt = a.g.Ns * a.nrhs;
+    int nb = (int)((nt + 127) / 128);
+    dslash_kernel<R, MINB><<<nb, 128, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
-template cudaError_t qs_dslash_launch<double>(DslashArgs<double>, int, cudaStream_t);
-template cudaError_t qs_dslash_launch<float>(DslashArgs<float>, int, cudaStream_t);
+// Launch-bound variants (minimum resident 128-thread blocks per SM); the
+// autotuner in capi.cu picks one per (precision, nrhs) by timing.
+template <>
+int qs_dslash_nvariants<float>() { return 5; }
+template <>
+int qs_dslash_nvariants<double>() { return 4; }
+
+template <>
+cudaError_t qs_dslash_launch<float>(DslashArgs<float> a, int nrhs, int variant, cudaStream_t st)
+{
+    a.nrhs = nrhs;
+    switch (variant) {
+    case 0: return launch_variant<float, 3>(a, st);
+    case 1: return launch_variant<float, 4>(a, st);
+    case 2: return launch_variant<float, 5>(a, st);
+    case 3: return launch_variant<float, 6>(a, st);
+    default: return launch_variant<float, 8>(a, st);
+    }
+}
+
+template <>
+cudaError_t qs_dslash_launch<double>(DslashArgs<double> a, int nrhs, int variant, cudaStream_t st)
+{
+    a.nrhs = nrhs;
+    switch (variant) {
+    case 0: return launch_variant<double, 1>(a, st);
+    case 1: return launch_variant<double, 2>(a, st);
+    case 2: return launch_variant<double, 3>(a, st);
+    default: return launch_variant<double, 4>(a, st);
+    }
+}

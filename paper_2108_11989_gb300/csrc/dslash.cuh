@@ -16,9 +16,18 @@ struct DslashArgs {
     const R *in;                          // [nrhs][Ns][24]
     R *out;
     int gamma5;                           // 1: Q = gamma_5 D
+    int nrhs;                             // right-hand sides in this launch
     double m0[QS_MAX_RHS];                // bare mass per right-hand side
 };
 
-// out = D in (or Q in) for nrhs vectors; in and out must not overlap.
+// out = D in (or Q in) for nrhs vectors with launch variant `variant`
+// (0 .. qs_dslash_nvariants<R>() - 1); in and out must not overlap.
 template <typename R>
-cudaError_t qs_dslash_launch(DslashArgs<R> a, int nrhs, cudaStream_t st);
+cudaError_t qs_dslash_launch(DslashArgs<R> a, int nrhs, int variant, cudaStream_t st);
+template <typename R>
+int qs_dslash_nvariants();
+
+// Picks (and caches in the handle) the fastest variant for this precision and
+// nrhs by timing each once on the handle's stream, then launches it.
+int qs_dslash_run(qs_lattice *lat, int prec, const double *m0, const void *in, void *out,
+                  int nrhs, int gamma5);

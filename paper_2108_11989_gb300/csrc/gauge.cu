@@ -167,6 +167,30 @@ __global__ void pack_links_kernel(Geom g, const double2 *su3, const double *th, 
     }
 }
 
+// max over physical sites and both chiral blocks of the Frobenius norm of the SW
+// term block (an upper bound of its spectral norm); the mirror block S conj(A) S
+// has the same norm.  Positive doubles order like their bit patterns.
+__global__ void clover_norm_kernel(Geom g, const double *clov, unsigned long long *out)
+{
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double m = 0;
+    if (p < g.Vphys) {
+        for (int b = 0; b < 2; ++b) {
+            double f = 0;
+            for (int i = 0; i < 6; ++i) {
+                double d = clov[(int64_t)(b * 36 + i) * g.Vphys + p];
+                f += d * d;
+            }
+            for (int k = 6; k < 36; ++k) {
+                double d = clov[(int64_t)(b * 36 + k) * g.Vphys + p];
+                f += 2 * d * d;
+            }
+            m = fmax(m, sqrt(f));
+        }
+    }
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 }  // namespace
 
 static void free_gauge(qs_lattice *lat)
@@ -210,7 +234,20 @@ extern "C" int qs_load_gauge(qs_lattice *lat, const double *su3, const double *u
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "clover_build_kernel"); break; }
         pack_links_kernel<<<nb, 128, 0, lat->stream>>>(g, d_su3, d_th, lat->links64, lat->links32);
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "pack_links_kernel"); break; }
+        unsigned long long *d_nm = (unsigned long long *)d_th;   // reuse after the builds
+        if (!d_nm) {
+            if ((e = cudaMalloc(&d_th, sizeof(double))) != cudaSuccess) { fail(e, "malloc norm"); break; }
+            d_nm = (unsigned long long *)d_th;
+        }
+        if ((e = cudaMemsetAsync(d_nm, 0, sizeof(unsigned long long), lat->stream)) != cudaSuccess) { fail(e, "memset"); break; }
+        clover_norm_kernel<<<nb, 128, 0, lat->stream>>>(g, lat->clov64, d_nm);
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "clover_norm_kernel"); break; }
+        unsigned long long hn = 0;
+        if ((e = cudaMemcpyAsync(&hn, d_nm, sizeof(hn), cudaMemcpyDeviceToHost, lat->stream)) != cudaSuccess) { fail(e, "copy norm"); break; }
         if ((e = cudaStreamSynchronize(lat->stream)) != cudaSuccess) { fail(e, "load_gauge sync"); break; }
+        double dn;
+        memcpy(&dn, &hn, sizeof(dn));
+        lat->clov_norm = dn;
     } while (0);
     cudaFree(d_su3);
     cudaFree(d_th);

@@ -42,6 +42,7 @@ struct qs_lattice {
     cudaStream_t stream;
     int gauge_loaded;
     double csw_su3, csw_u1;
+    double clov_norm;      // max over sites of ||A(x)||_F (bounds ||A(x)||)
     // V = U exp(i theta) on the physical lattice, SoA [mu][9][Vphys] complex
     double2 *links64;
     float2 *links32;
@@ -49,6 +50,10 @@ struct qs_lattice {
     // Hermitian blocks); the mirror site's blocks are derived on the fly
     double *clov64;
     float *clov32;
+    // autotuned Dslash launch variant + 1 per [precision][nrhs] (0: not tuned yet)
+    int tuned[2][65];
+    // solver workspace (allocated on first use, see solver.cu)
+    struct Workspace *ws;
 };
 
 // neighbour of doubled site s in direction mu, step +1/-1; *sgn = fermion bc factor

@@ -1,0 +1,415 @@
+// Low modes of Q(m0) and the Pfaffian sign by the mass flow (Sec. 3).
+//
+// lowmodes: block subspace iteration, Rayleigh-Ritz of the FP64 Q.
+//   * filter pass: Y = C_d(Q^2) V with the scaled Chebyshev recurrence on the
+//     interval [theta_k^2, b] (b >= lambda_max(Q^2)), FP32 storage and arithmetic;
+//   * refinement pass: one power step with Q^-2 (the operator Sec. 3 names),
+//     W = Q^-2 V by CG on Q^2 with FP32 inner iterations and FP64 defect
+//     correction, started from V Theta^-2;
+//   * orthonormalisation: column scaling + Cholesky-QR twice, FP64;
+//   * Rayleigh-Ritz: H = V^H Q V, Jacobi, rotate V and QV, residuals in FP64.
+#include "blas.cuh"
+#include "dslash.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <time.h>
+
+#include <algorithm>
+#include <vector>
+
+struct Workspace {
+    int k;
+    int64_t nr;
+    double *blk64[6];     // FP64 blocks [k][nr]
+    float *blk32[5];      // FP32 blocks [k][nr]
+    double *part;         // reduction partials
+    double2 *G, *Rinv, *Hm, *Ym;
+    double *ds;           // device scalars, S_NSLOT slots of 64
+    int *di;              // device ints, 64 + 8
+    double *hp;           // pinned host mirror of ds (S_NSLOT x 64)
+    int *hi;              // pinned host ints (64 + 8)
+    int vi;               // index of the block holding the current subspace V
+    int have_V;
+    int64_t f32_count, f64_count, cg_count;
+};
+
+#define DS(ws, slot) ((ws)->ds + 64 * (slot))
+enum { S_TMP = 0, S_THETA = 1, S_COEF = 2, S_RR = 3, S_RR0 = 4, S_PAP = 5, S_BETA = 6, S_ONES = 7, S_RN = 8,
+       S_NSLOT = 12 };
+
+static void ws_free(Workspace *w)
+{
+    if (!w) return;
+    for (int i = 0; i < 6; ++i) cudaFree(w->blk64[i]);
+    for (int i = 0; i < 5; ++i) cudaFree(w->blk32[i]);
+    cudaFree(w->part); cudaFree(w->G); cudaFree(w->Rinv); cudaFree(w->Hm); cudaFree(w->Ym);
+    cudaFree(w->ds); cudaFree(w->di);
+    cudaFreeHost(w->hp); cudaFreeHost(w->hi);
+    free(w);
+}
+
+void qs_free_workspace(qs_lattice *lat)
+{
+    ws_free(lat->ws);
+    lat->ws = nullptr;
+}
+
+#define CK(call)                                                           \
+    do {                                                                   \
+        cudaError_t _e = (call);                                           \
+        if (_e != cudaSuccess) {                                           \
+            qs_record_cuda_error(_e, #call);                               \
+            return _e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA; \
+        }                                                                  \
+    } while (0)
+
+static int ws_get(qs_lattice *lat, int k, Workspace **out)
+{
+    Workspace *w = lat->ws;
+    if (w && w->k == k) { *out = w; return QS_OK; }
+    qs_free_workspace(lat);
+    w = (Workspace *)calloc(1, sizeof(Workspace));
+    if (!w) return QS_ENOMEM;
+    lat->ws = w;
+    w->k = k;
+    w->nr = lat->g.Ns * 24;
+    size_t n64 = (size_t)k * w->nr * sizeof(double), n32 = (size_t)k * w->nr * sizeof(float);
+    for (int i = 0; i < 6; ++i) CK(cudaMalloc(&w->blk64[i], n64));
+    for (int i = 0; i < 5; ++i) CK(cudaMalloc(&w->blk32[i], n32));
+    CK(cudaMalloc(&w->part, (size_t)QS_RED_BLOCKS * 2 * 64 * 64 * sizeof(double)));
+    CK(cudaMalloc(&w->G, 64 * 64 * sizeof(double2)));
+    CK(cudaMalloc(&w->Rinv, 64 * 64 * sizeof(double2)));
+    CK(cudaMalloc(&w->Hm, 64 * 64 * sizeof(double2)));
+    CK(cudaMalloc(&w->Ym, 64 * 64 * sizeof(double2)));
+    CK(cudaMalloc(&w->ds, S_NSLOT * 64 * sizeof(double)));
+    CK(cudaMalloc(&w->di, 72 * sizeof(int)));
+    CK(cudaMallocHost(&w->hp, S_NSLOT * 64 * sizeof(double)));
+    CK(cudaMallocHost(&w->hi, 72 * sizeof(int)));
+    CK(cudaMemsetAsync(w->di, 0, 72 * sizeof(int), lat->stream));
+    for (int i = 0; i < 64; ++i) w->hp[i] = 1.0;
+    CK(cudaMemcpyAsync(DS(w, S_ONES), w->hp, 64 * sizeof(double), cudaMemcpyHostToDevice, lat->stream));
+    CK(cudaStreamSynchronize(lat->stream));
+    w->vi = 0;
+    w->have_V = 0;
+    *out = w;
+    return QS_OK;
+}
+
+// ---- operator helpers ---------------------------------------------------------
+static int opQ(qs_lattice *lat, Workspace *w, int prec, double m0, const void *in, void *out, int k)
+{
+    double m[QS_MAX_RHS];
+    for (int r = 0; r < k; ++r) m[r] = m0;
+    if (prec == QS_F32) w->f32_count += k; else w->f64_count += k;
+    return qs_dslash_run(lat, prec, m, in, out, k, 1);
+}
+
+static int opQ2(qs_lattice *lat, Workspace *w, int prec, double m0, const void *in, void *tmp, void *out, int k)
+{
+    QS_TRY(opQ(lat, w, prec, m0, in, tmp, k));
+    return opQ(lat, w, prec, m0, tmp, out, k);
+}
+
+static int sync_read(qs_lattice *lat, Workspace *w, int slot, int n)
+{
+    CK(cudaMemcpyAsync(w->hp + 64 * slot, DS(w, slot), n * sizeof(double), cudaMemcpyDeviceToHost, lat->stream));
+    CK(cudaMemcpyAsync(w->hi, w->di, 72 * sizeof(int), cudaMemcpyDeviceToHost, lat->stream));
+    CK(cudaStreamSynchronize(lat->stream));
+    return QS_OK;
+}
+
+// column scaling + Cholesky-QR twice: X becomes orthonormal (tmp is clobbered)
+static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp, int k)
+{
+    cudaStream_t st = lat->stream;
+    CK(qs_norm2<double>(X, k, w->nr, w->part, DS(w, S_TMP), st));
+    CK(qs_map_scalars(DS(w, S_TMP), DS(w, S_COEF), k, 0, st));
+    CK(qs_scale_cols(X, DS(w, S_COEF), k, w->nr, st));
+    for (int pass = 0; pass < 2; ++pass) {
+        double *src = pass == 0 ? X : tmp, *dst = pass == 0 ? tmp : X;
+        CK(qs_gram(src, k, src, k, w->nr, w->part, w->G, st));
+        CK(qs_chol_rinv(w->G, k, w->Rinv, w->di + 64 + pass, st));
+        CK(qs_rotate(src, k, w->Rinv, k, w->nr, dst, st));
+    }
+    return QS_OK;
+}
+
+// Rayleigh-Ritz on the orthonormal block V = blk64[0], in two stages.
+// (1) Q^2 stage: H2 = (QV)^H (QV), V <- V Y ordered by the Q^2 Ritz values mu.  The
+//     wanted |lambda| are the lowest of Q^2, an end of its spectrum, so this stage
+//     has no spurious Ritz values (a Rayleigh-Ritz with the indefinite Q can pair
+//     +lambda and -lambda contaminations into a small, meaningless theta).
+// (2) Q stage on the leading kc = k - 2 columns: signed Ritz values theta of Q,
+//     sorted by |theta|; the last two columns keep theta = <v, Q v>.
+// Afterwards blk64[0] = V, blk64[1] = Q V; theta, residuals ||Q v - theta v|| and
+// mu are on the host.
+static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *rz)
+{
+    cudaStream_t st = lat->stream;
+    const int kc = k - 2;
+    const size_t colb = (size_t)w->nr * sizeof(double);
+    QS_TRY(opQ(lat, w, QS_F64, m0, w->blk64[0], w->blk64[1], k));
+    // (1) Q^2 stage
+    CK(qs_gram(w->blk64[1], k, w->blk64[1], k, w->nr, w->part, w->Hm, st));
+    CK(qs_herm_eig(w->Hm, k, DS(w, S_TMP), w->Ym, w->di + 66, st));
+    CK(qs_rotate(w->blk64[0], k, w->Ym, k, w->nr, w->blk64[2], st));
+    CK(qs_rotate(w->blk64[1], k, w->Ym, k, w->nr, w->blk64[3], st));
+    std::swap(w->blk64[0], w->blk64[2]);
+    std::swap(w->blk64[1], w->blk64[3]);
+    CK(cudaMemcpyAsync(rz->mu, DS(w, S_TMP), k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // (2) Q stage on the leading kc columns
+    CK(qs_gram(w->blk64[0], kc, w->blk64[1], kc, w->nr, w->part, w->Hm, st));
+    CK(qs_herm_eig(w->Hm, kc, DS(w, S_THETA), w->Ym, w->di + 67, st));
+    CK(qs_rotate(w->blk64[0], kc, w->Ym, kc, w->nr, w->blk64[2], st));
+    CK(qs_rotate(w->blk64[1], kc, w->Ym, kc, w->nr, w->blk64[3], st));
+    CK(cudaMemcpyAsync(w->blk64[2] + (size_t)kc * w->nr, w->blk64[0] + (size_t)kc * w->nr, (k - kc) * colb,
+                       cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(w->blk64[3] + (size_t)kc * w->nr, w->blk64[1] + (size_t)kc * w->nr, (k - kc) * colb,
+                       cudaMemcpyDeviceToDevice, st));
+    std::swap(w->blk64[0], w->blk64[2]);
+    std::swap(w->blk64[1], w->blk64[3]);
+    // theta of the trailing columns: <v, Q v>
+    CK(qs_dot<double>(w->blk64[0] + (size_t)kc * w->nr, w->blk64[1] + (size_t)kc * w->nr, k - kc, w->nr,
+                      w->part, DS(w, S_COEF), st));
+    QS_TRY(sync_read(lat, w, S_COEF, 2 * (k - kc)));
+    for (int i = kc; i < k; ++i) w->hp[64 * S_TMP + i] = w->hp[64 * S_COEF + 2 * (i - kc)];
+    CK(cudaMemcpyAsync(DS(w, S_THETA) + kc, w->hp + 64 * S_TMP + kc, (k - kc) * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    CK(qs_resid2(w->blk64[1], w->blk64[0], DS(w, S_THETA), k, w->nr, w->part, DS(w, S_TMP), st));
+    CK(cudaMemcpyAsync(w->hp + 64 * S_THETA, DS(w, S_THETA), k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QS_TRY(sync_read(lat, w, S_TMP, k));
+    if (w->hi[64] || w->hi[65]) return QS_ENUMERIC;   // Cholesky-QR broke down
+    for (int i = 0; i < k; ++i) {
+        rz->theta[i] = w->hp[64 * S_THETA + i];
+        double r2 = w->hp[64 * S_TMP + i];
+        rz->res[i] = sqrt(r2 > 0 ? r2 : 0);
+        if (!isfinite(rz->theta[i]) || !isfinite(rz->res[i])) return QS_ENUMERIC;
+    }
+    return QS_OK;
+}
+
+// Chebyshev filter of degree d on Q^2 over [a, b], FP32: blk32[0] (in) -> result
+// in *res (one of blk32); scaled three-term recurrence (values at 0 kept O(1))
+static int cheb_filter(qs_lattice *lat, Workspace *w, double m0, int k, int d, double a, double b, float **res)
+{
+    cudaStream_t st = lat->stream;
+    float *X = w->blk32[0], *Y = w->blk32[1], *Yn = w->blk32[2], *T = w->blk32[3], *AY = w->blk32[4];
+    int64_t n = (int64_t)k * w->nr;
+    double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    double sigma1 = e / (0.0 - c);
+    double sigma = sigma1, g = 2.0 / sigma1;
+    QS_TRY(opQ2(lat, w, QS_F32, m0, X, T, AY, k));
+    CK(qs_cheb_step<float>(Y, AY, X, X, c, sigma1 / e, 0.0, n, st));
+    for (int i = 2; i <= d; ++i) {
+        double s2 = 1.0 / (g - sigma);
+        QS_TRY(opQ2(lat, w, QS_F32, m0, Y, T, AY, k));
+        CK(qs_cheb_step<float>(Yn, AY, Y, X, c, 2.0 * s2 / e, sigma * s2, n, st));
+        float *tmp = X; X = Y; Y = Yn; Yn = tmp;
+        sigma = s2;
+    }
+    // keep the buffer roles consistent for the caller: result pointer
+    *res = Y;
+    return QS_OK;
+}
+
+// FP32 CG on Q^2 for k right-hand sides in r (overwritten); solution in x.
+static int cg_f32(qs_lattice *lat, Workspace *w, double m0, int k, float *x, float *r, float *p, float *t,
+                  float *ap, double tol, int maxit, int *iters)
+{
+    cudaStream_t st = lat->stream;
+    CgScalars s;
+    s.rr = DS(w, S_RR); s.rr0 = DS(w, S_RR0); s.pap = DS(w, S_PAP); s.beta = DS(w, S_BETA);
+    s.active = w->di;
+    size_t bytes = (size_t)k * w->nr * sizeof(float);
+    CK(cudaMemsetAsync(x, 0, bytes, st));
+    CK(cudaMemcpyAsync(p, r, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(qs_norm2<float>(r, k, w->nr, w->part, DS(w, S_TMP), st));
+    CK(qs_cg_init(s, DS(w, S_TMP), k, st));
+    int it;
+    for (it = 1; it <= maxit; ++it) {
+        QS_TRY(opQ(lat, w, QS_F32, m0, p, t, k));
+        QS_TRY(opQ(lat, w, QS_F32, m0, t, ap, k));
+        CK(qs_norm2<float>(t, k, w->nr, w->part, s.pap, st));        // <p, Q^2 p> = |Q p|^2
+        CK(qs_cg_update(x, r, p, ap, s, k, w->nr, w->part, st));
+        CK(qs_cg_finalize(s, tol * tol, k, w->part, w->di + 70, st));
+        CK(qs_cg_pupdate(p, r, s, k, w->nr, st));
+        if (it % 16 == 0 || it == maxit) {
+            CK(cudaMemcpyAsync(w->hi + 70, w->di + 70, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (w->hi[70] == 0) break;
+        }
+    }
+    w->cg_count += it;
+    *iters = it;
+    return QS_OK;
+}
+
+static int verbose()
+{
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("QS_VERBOSE");
+        v = e ? atoi(e) : 0;
+    }
+    return v;
+}
+
+// X (initial guess in, solution out) of Q^2 X = B for orthonormal B, by FP32 CG
+// inner solves and FP64 residuals; stops when every ||B - Q^2 X|| <= tol.
+static int solve_q2_mixed(qs_lattice *lat, Workspace *w, double m0, int k, const double *B, double *X,
+                          double *T1, double *T2, double tol)
+{
+    cudaStream_t st = lat->stream;
+    for (int outer = 0; outer < 40; ++outer) {
+        QS_TRY(opQ2(lat, w, QS_F64, m0, X, T1, T2, k));
+        CK(qs_axpby<double>(1.0, B, -1.0, T2, (int64_t)k * w->nr, st));       // T2 = B - Q^2 X
+        CK(qs_norm2<double>(T2, k, w->nr, w->part, DS(w, S_RN), st));
+        QS_TRY(sync_read(lat, w, S_RN, k));
+        double rmax = 0;
+        for (int i = 0; i < k; ++i) rmax = std::max(rmax, sqrt(w->hp[64 * S_RN + i]));
+        if (verbose() > 1) fprintf(stderr, "[qstar]   solve outer %d max|r| %.3e (target %.3e)\n", outer, rmax, tol);
+        if (rmax <= tol) return QS_OK;
+        CK(qs_map_scalars(DS(w, S_RN), DS(w, S_COEF), k, 0, st));             // 1 / |r|
+        CK(qs_d2f(T2, w->blk32[0], DS(w, S_COEF), k, w->nr, st));
+        double tin = std::max(2e-6, std::min(0.1, 0.3 * tol / rmax));
+        int its = 0;
+        QS_TRY(cg_f32(lat, w, m0, k, w->blk32[1], w->blk32[0], w->blk32[2], w->blk32[3], w->blk32[4], tin,
+                      20000, &its));
+        if (verbose() > 1) fprintf(stderr, "[qstar]   inner CG %d iterations (tol %.2e)\n", its, tin);
+        CK(qs_map_scalars(DS(w, S_RN), DS(w, S_COEF), k, 1, st));             // |r|
+        CK(qs_axpy_f2d(X, w->blk32[1], DS(w, S_COEF), k, w->nr, st));
+    }
+    return QS_ENOCONV;
+}
+
+static double now_s()
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return ts.tv_sec + 1e-9 * ts.tv_nsec;
+}
+
+extern "C" void qs_eig_default_opts(qs_eig_opts *o)
+{
+    if (!o) return;
+    o->k = 16;
+    o->nwant = 4;
+    o->tol = 1e-8;
+    o->max_iter = 200;
+    o->cheb_degree = 24;
+    o->warm_start = 1;
+    o->seed = 1;
+}
+
+
+int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz, int *conv, qs_eig_stats *stats)
+{
+    int k = o->k;
+    Workspace *w;
+    QS_TRY(ws_get(lat, k, &w));
+    cudaStream_t st = lat->stream;
+    double t0 = now_s();
+    int64_t f32_0 = w->f32_count, f64_0 = w->f64_count, cg_0 = w->cg_count;
+    if (!(o->warm_start && w->have_V)) {
+        CK(qs_fill_gauss(w->blk64[0], (int64_t)k * w->nr, o->seed * 0x9E3779B97F4A7C15ULL + 17, st));
+    }
+    w->have_V = 0;
+    QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k));
+    QS_TRY(rayleigh_ritz(lat, w, m0, k, rz));
+    // b >= lambda_max(Q^2): ||Q|| = ||D|| <= max_x ||4 + m0 + A(x)|| + ||hopping||,
+    // ||hopping|| <= 4 (each direction is a partial isometry pair of norm 1)
+    double qn = fabs(4.0 + m0) + lat->clov_norm + 4.0;
+    double b = qn * qn;
+    int it = 0, nf = 0, nref = 0;
+    *conv = 0;
+    double prev_worst = 1e300;
+    int stall = 0, fstall = 0;
+    for (it = 0; it < o->max_iter; ++it) {
+        double worst = 0;
+        for (int i = 0; i < o->nwant; ++i)
+            worst = std::max(worst, rz->res[i] / std::max(fabs(rz->theta[i]), 1e-300));
+        // Filter while it makes progress and the block is far from converged; then
+        // power steps with Q^-2, whose rate (lambda_i / lambda_{k+1})^2 does not
+        // depend on how small lambda_bar is.  The FP32 filter cannot improve a block
+        // below ~1e-5 relative residual, so only a stagnating refinement hands back.
+        bool refine = (worst < 1e-3 || fstall >= 2) && !(stall >= 3 && worst > 1e-5);
+        if (verbose())
+            fprintf(stderr, "[qstar] m0=%.6f pass %d worst_rel_res=%.3e theta0=%.6e res0=%.3e theta_k=%.4e b=%.3e next=%s\n",
+                    m0, it, worst, rz->theta[0], rz->res[0], rz->theta[k - 1], b,
+                    worst <= o->tol ? "done" : (refine ? "refine" : "filter"));
+        if (worst <= o->tol) { *conv = 1; break; }
+        if (!refine) {
+            // Chebyshev filter on [a, b], a = largest Q^2 Ritz value of the block
+            double a = rz->mu[k - 1];
+            if (a >= 0.5 * b || it == 0) a = std::min(a, 0.05 * b);
+            CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
+            float *Y = nullptr;
+            QS_TRY(cheb_filter(lat, w, m0, k, std::max(2, o->cheb_degree), a, b, &Y));
+            CK(cudaMemsetAsync(w->blk64[2], 0, (size_t)k * w->nr * sizeof(double), st));
+            CK(qs_axpy_f2d(w->blk64[2], Y, DS(w, S_ONES), k, w->nr, st));
+            std::swap(w->blk64[0], w->blk64[2]);
+            ++nf;
+        } else {
+            // power step with Q^-2: X = Q^-2 V, started from V_i / <v_i, Q^2 v_i>
+            // (<v, Q^2 v> = theta^2 + r^2 for each Ritz vector)
+            double inv[64];
+            for (int i = 0; i < k; ++i) {
+                double q2 = rz->theta[i] * rz->theta[i] + rz->res[i] * rz->res[i];
+                inv[i] = q2 > 0 ? 1.0 / q2 : 0.0;
+            }
+            CK(cudaMemcpyAsync(DS(w, S_COEF), inv, k * sizeof(double), cudaMemcpyHostToDevice, st));
+            CK(qs_scaled_copy(w->blk64[2], w->blk64[0], DS(w, S_COEF), k, w->nr, st));
+            // solve accuracy tied to the absolute residual the target needs
+            double tsol = std::max(1e-13, std::min(1e-2, 0.05 * worst * fabs(rz->theta[0])));
+            int s = solve_q2_mixed(lat, w, m0, k, w->blk64[0], w->blk64[2], w->blk64[4], w->blk64[5], tsol);
+            if (s != QS_OK && s != QS_ENOCONV) return s;
+            std::swap(w->blk64[0], w->blk64[2]);
+            ++nref;
+        }
+        QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k));
+        QS_TRY(rayleigh_ritz(lat, w, m0, k, rz));
+        double nw = 0;
+        for (int i = 0; i < o->nwant; ++i)
+            nw = std::max(nw, rz->res[i] / std::max(fabs(rz->theta[i]), 1e-300));
+        if (refine && nw > 0.97 * prev_worst) ++stall; else stall = 0;
+        if (!refine && nw > 0.9 * prev_worst) ++fstall; else if (!refine) fstall = 0;
+        prev_worst = nw;
+    }
+    w->have_V = 1;
+    if (stats) {
+        stats->iterations = it;
+        stats->filter_passes = nf;
+        stats->refine_passes = nref;
+        stats->dslash_f32 = w->f32_count - f32_0;
+        stats->dslash_f64 = w->f64_count - f64_0;
+        stats->cg_iterations = w->cg_count - cg_0;
+        stats->seconds = now_s() - t0;
+    }
+    return QS_OK;
+}
+
+extern "C" int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts *opts, double *evals,
+                                   double *resid, void *evecs, qs_eig_stats *stats)
+{
+    if (!lat || !evals || !resid) return QS_EINVAL;
+    if (!lat->gauge_loaded) return QS_EINVAL;
+    qs_eig_opts o;
+    if (opts) o = *opts; else qs_eig_default_opts(&o);
+    if (o.k < 2 || o.k > 64 || (o.k & 1) || o.nwant < 1 || o.nwant > o.k || !(o.tol > 0) || o.max_iter < 0 ||
+        o.cheb_degree < 2)
+        return QS_EINVAL;
+    if (12 * lat->g.Ns < o.k) return QS_EINVAL;
+    CK(cudaSetDevice(lat->device));
+    Ritz rz;
+    int conv = 0;
+    QS_TRY(qs_lowmodes_impl(lat, m0, &o, &rz, &conv, stats));
+    for (int i = 0; i < o.k; ++i) { evals[i] = rz.theta[i]; resid[i] = rz.res[i]; }
+    if (evecs) {
+        CK(cudaMemcpyAsync(evecs, lat->ws->blk64[0], (size_t)o.k * lat->ws->nr * sizeof(double),
+                           cudaMemcpyDeviceToDevice, lat->stream));
+        CK(cudaStreamSynchronize(lat->stream));
+    }
+    return conv ? QS_OK : QS_ENOCONV;
+}

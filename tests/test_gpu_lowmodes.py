@@ -1,0 +1,88 @@
+"""Low eigenvalues of Q (qs_lowmodes_at_mass through the C-ABI) against the oracle.
+
+Tolerance: 1e-10 relative on every wanted eigenvalue (FP64 Rayleigh-Ritz), and
+each reported residual must bound the distance to a true eigenvalue.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from synth_inputs import WORKLOADS, kappa_to_m0, make_config
+from oracle.dirac import WilsonDirac
+from oracle.lowmodes import modes_dense
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import paper_2108_11989_gb300 as qs
+    return qs
+
+
+def lattice(qs, cfg):
+    lat = qs.Lattice(cfg.L, cfg.T, cfg.cstar_mask, cfg.t_antiperiodic)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    return lat
+
+
+def check_against(ev, rs, ref, nwant, rtol=1e-10):
+    ref_sorted = ref[np.argsort(np.abs(ref), kind="stable")]
+    for i in range(nwant):
+        j = np.argmin(np.abs(ref_sorted - ev[i]))
+        assert abs(ev[i] - ref_sorted[j]) <= rtol * abs(ref_sorted[j]) + 1e-14, (i, ev[i], ref_sorted[j])
+        assert abs(ev[i] - ref_sorted[j]) <= rs[i] + 1e-12
+    # the wanted Ritz values are the smallest |lambda| (pairs counted twice)
+    assert np.allclose(np.sort(np.abs(ev[:nwant])), np.abs(ref_sorted[:nwant]), rtol=rtol, atol=1e-14)
+
+
+@pytest.mark.parametrize("m0", [-0.6, 0.1])
+def test_small_rough_lattice_dense_reference(qs, m0):
+    cfg = make_config(T=4, L=2, eps=0.9, theta_sigma=0.4, csw_su3=1.3, csw_u1=0.8, seed=5)
+    lat = lattice(qs, cfg)
+    opts = qs.eig_default_opts(k=16, nwant=8, tol=1e-9, cheb_degree=16)
+    ev, rs, st = lat.lowmodes_at_mass(m0, opts)
+    ref = np.linalg.eigvalsh(WilsonDirac(cfg).dense_Q(m0))
+    check_against(ev, rs, ref, 8)
+    lat.close()
+
+
+def test_tiny_workload_golden(qs):
+    """4^4 workload: the 8 lowest |lambda| at the 4 golden masses (dense oracle values)."""
+    g = json.load(open(os.path.join(HERE, "golden", "tiny_4x4x4x4_seed0.json")))
+    cfg = make_config(seed=0, **WORKLOADS["tiny_4x4x4x4"])
+    lat = lattice(qs, cfg)
+    opts = qs.eig_default_opts(k=16, nwant=8, tol=1e-9, cheb_degree=24)
+    for pt in g["points"]:
+        ev, rs, st = lat.lowmodes_at_mass(pt["m0"], opts)
+        ref = np.array(pt["lowest_abs_sorted_eigs_Q"])
+        check_against(ev, rs, ref, 8)
+    lat.close()
+
+
+def test_pairs_are_degenerate(qs):
+    cfg = make_config(T=4, L=4, eps=0.5, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=2)
+    lat = lattice(qs, cfg)
+    ev, rs, st = lat.lowmodes_at_mass(-0.2, qs.eig_default_opts(k=16, nwant=8, tol=1e-9))
+    s = np.sort(ev[:8])
+    assert np.allclose(s[0::2], s[1::2], rtol=1e-9, atol=1e-13)
+    lat.close()
+
+
+def test_eigenvectors_returned(qs):
+    import torch
+    cfg = make_config(T=4, L=2, eps=0.9, theta_sigma=0.4, csw_su3=1.3, csw_u1=0.8, seed=5)
+    lat = lattice(qs, cfg)
+    k = 8
+    V = torch.zeros(k * cfg.n_sites * 24, dtype=torch.float64, device="cuda")
+    ev, rs, st = lat.lowmodes_at_mass(-0.6, qs.eig_default_opts(k=k, nwant=4, tol=1e-9), evecs=V)
+    v = V.cpu().numpy().view(np.complex128).reshape(k, -1)
+    op = WilsonDirac(cfg)
+    for i in range(4):
+        r = op.apply_Q(v[i], -0.6) - ev[i] * v[i]
+        assert np.linalg.norm(r) <= 1e-8 * abs(ev[i]) + 1e-12
+        assert abs(np.linalg.norm(v[i]) - 1) < 1e-12
+    lat.close()

@@ -1,0 +1,63 @@
+"""Pfaffian sign through the C-ABI (qs_pfaffian_sign) against the oracle: bit-exact."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from synth_inputs import WORKLOADS, make_config
+from oracle.dirac import WilsonDirac
+from oracle.sign import sign_by_eigencount
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import paper_2108_11989_gb300 as qs
+    return qs
+
+
+def lattice(qs, cfg):
+    lat = qs.Lattice(cfg.L, cfg.T, cfg.cstar_mask, cfg.t_antiperiodic)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    return lat
+
+
+def test_rough_small_lattice_negative_signs(qs):
+    cfg = make_config(T=4, L=2, eps=2.0, theta_sigma=0.3, csw_su3=1.5, csw_u1=1.0, seed=2)
+    op = WilsonDirac(cfg)
+    lat = lattice(qs, cfg)
+    opts = qs.sign_default_opts(eig={"k": 16, "nwant": 2, "tol": 1e-6, "cheb_degree": 16})
+    got = []
+    for m in [-2.05, -1.85, -1.65, -1.5, 0.3]:
+        ref = sign_by_eigencount(op, m)
+        s, rep = lat.pfaffian_sign(m, opts)
+        assert s == ref, (m, s, ref, rep["phase"])
+        got.append(s)
+    assert -1 in got
+    lat.close()
+
+
+def test_tiny_workload_golden_signs(qs):
+    """4^4 workload at the 4 golden masses (dense Pfaffian and eigen-count agree)."""
+    g = json.load(open(os.path.join(HERE, "golden", "tiny_4x4x4x4_seed0.json")))
+    cfg = make_config(seed=0, **WORKLOADS["tiny_4x4x4x4"])
+    lat = lattice(qs, cfg)
+    opts = qs.sign_default_opts(eig={"k": 16, "nwant": 2, "tol": 1e-6, "cheb_degree": 24})
+    signs = []
+    for pt in g["points"]:
+        s, rep = lat.pfaffian_sign(pt["m0"], opts)
+        assert s == pt["sign"], (pt["m0"], s, pt["sign"], rep["phase"])
+        signs.append(s)
+    assert -1 in signs
+    lat.close()
+
+
+def test_large_mass_is_positive_in_one_step(qs):
+    cfg = make_config(T=4, L=4, eps=0.5, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=3)
+    lat = lattice(qs, cfg)
+    s, rep = lat.pfaffian_sign(3 * (1.9 + 1.0) + 0.5, qs.sign_default_opts())
+    assert s == 1 and rep["n"] == 1
+    lat.close()
