@@ -146,7 +146,8 @@ QS_API int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts *op
  *  step A (Sec. 3, steps 1-5): m <- m + c lambda_bar while lambda_bar does not
  *    decrease; stop with the sign found so far once m > m0_max.  Each step is
  *    certified by |lambda'| <= 1 (eq. derivativebound) with lower bounds
- *    lambda_bar - r: (lb_n - r_n) + (lb_{n+1} - r_{n+1}) >= m_{n+1} - m_n.
+ *    lambda_bar - r: (lb_n - r_n) + (lb_{n+1} - r_{n+1}) >= m_{n+1} - m_n; a step
+ *    that fails it is shortened to m_n + 0.95 (lb_n - r_n).
  *  step B (the paper defers it to other work; our reading): from the last
  *    certified mass, step by dm inside a spectral gap (a - dm, a + dm) of the
  *    tracked window and add the change of the number of eigenvalues in (-a, 0);
@@ -172,6 +173,10 @@ typedef struct {
     int64_t dslash_f32, dslash_f64;
     int64_t cg_iterations;
     double seconds;
+    int fail_reason;   /* 0 ok; 1 an eigensolve missed its tolerance; 2 step B found no
+                          spectral gap; 3 a step-B count was not certified (bounds straddle
+                          the gap, or the window does not reach above it); 4 odd change of
+                          the negative count; 5 max_steps reached; 6 lambda_bar - r <= 0 */
 } qs_sign_report;
 
 /* Fill *opts with defaults (c = 1.9, m0_max = 0 (auto), max_steps = 400, eig defaults
@@ -183,6 +188,32 @@ QS_API void qs_sign_default_opts(qs_sign_opts *opts);
  * the flow exceeds max_steps or an eigensolve does not converge. */
 QS_API int qs_pfaffian_sign(qs_lattice *lat, double m0_target, const qs_sign_opts *opts, int *sign,
                             qs_sign_report *report);
+
+/* ---------------------------------------------------------------------------
+ * Kernel profiling (measurement support, no counterpart in the paper).  While on,
+ * every operator launch of the handle is bracketed by CUDA events on the handle's
+ * stream; qs_get_profile synchronises the stream and reports per precision the
+ * launches, their summed device time and their algorithmic bytes (per doubled site:
+ * 48 spinor reals per right-hand side + 72 link and SW-term reals per launch).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t launches;
+    double ms;        /* summed event time of the launches */
+    double bytes;     /* summed algorithmic bytes */
+} qs_kernel_prof;
+
+typedef struct {
+    qs_kernel_prof dslash[2];   /* [QS_F64], [QS_F32] */
+} qs_profile;
+
+/* on = 1 starts (and zeroes) the counters, on = 0 stops recording. */
+QS_API int qs_set_profiling(qs_lattice *lat, int on);
+
+/* Resolve the recorded events into *prof (synchronises the stream). */
+QS_API int qs_get_profile(qs_lattice *lat, qs_profile *prof);
+
+/* Number of CUDA kernels this library has launched in this process (all handles). */
+QS_API int64_t qs_kernel_launches(void);
 
 /* Static description of a status code. */
 QS_API const char *qs_strerror(int status);

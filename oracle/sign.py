@@ -11,9 +11,11 @@ Three routes, all FP64 on the CPU:
 2. ``sign_by_eigencount``: pf[CTD] = prod_{n=1}^{12V} lambda_n (Sec. 3), one lambda per
    degenerate pair, so W_sgn = (-1)^(N_-/2) with N_- the number of negative
    eigenvalues of the dense Q counted with multiplicity.
-3. ``pfaffian_sign_flow``: the mass-flow algorithm.  Step A exactly as the
-   enumerated algorithm of Sec. 3 (steps 1-5, c slightly below 2), with each
-   certification made with lower bounds lambda_bar - ||r||.  Step B is not
+3. ``pfaffian_sign_flow``: the mass-flow algorithm.  Step A as the enumerated
+   algorithm of Sec. 3 (steps 1-5, c slightly below 2), each certification made with
+   lower bounds lambda_bar - ||r||; a step that leaves the crossing-free interval
+   (m - lambda_bar, m + lambda_bar) of eq. derivativebound uncovered is shortened to
+   its edge (m + 0.95 (lambda_bar - r)) instead of being accepted.  Step B is not
    described in the paper (it cites other work); our reading: from the last
    certified mass, walk upward in steps dm chosen inside a spectral gap of the
    tracked window (gap between sorted |lambda|: s_i < a < s_{i+1},
@@ -95,27 +97,29 @@ def pfaffian_sign_flow(modes_fn, m_target, m0_max, c=1.9, max_steps=200, min_ste
     steps = 0
     while steps < max_steps:
         # ---- step A (steps 1-5 of the enumerated algorithm) ----------------
-        n = 0
-        prev = None
         go_b = False
         while steps < max_steps:
             lb, rb = _lambda_bar(cur)
-            if n >= 1:
-                plb, prb = prev
-                covered = (plb - prb) + (lb - rb) >= (m - pm)
-                if lb < plb or not covered:          # step 3 (or a cover failure)
-                    go_b = True
-                    if not covered:                   # restart B from the last covered mass
-                        m, cur = pm, pcur
-                    break
             if m > m0_max or m + (lb - rb) > m0_max:   # step 4 (or its interval covers m0_max)
                 return (1 if flips % 2 == 0 else -1), report
-            pm, pcur, prev = m, cur, (lb, rb)
-            m = m + c * lb                           # step 5
-            cur = modes(m)
+            m_new = m + c * lb                           # step 5
+            new = modes(m_new)
             report["phase"].append("A")
-            n += 1
             steps += 1
+            lb2, rb2 = _lambda_bar(new)
+            covered = (lb - rb) + (lb2 - rb2) >= (m_new - m)
+            if not covered:
+                # the step went past the interval (m - lb, m + lb) of eq. derivativebound
+                # that is free of crossings: retreat to its edge
+                m_new = m + 0.95 * (lb - rb)
+                new = modes(m_new)
+                report["phase"].append("A")
+                steps += 1
+                lb2, rb2 = _lambda_bar(new)
+            m, cur = m_new, new
+            if lb2 < lb:                                 # step 3: lambda_bar decreases
+                go_b = True
+                break
         if not go_b:
             break
         # ---- step B (our reading, see module doc) --------------------------

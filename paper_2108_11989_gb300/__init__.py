@@ -14,6 +14,7 @@ from .build import LIB
 
 __all__ = ["QStarError", "Lattice", "create_lattice", "load_gauge", "apply_Dw", "apply_Q",
            "lowmodes_at_mass", "pfaffian_sign", "eig_default_opts", "sign_default_opts",
+           "set_profiling", "get_profile",
            "strerror", "QS_F64", "QS_F32", "lib"]
 
 QS_F64, QS_F32 = 0, 1
@@ -58,7 +59,8 @@ class SignReport(ctypes.Structure):
                 ("phase", ctypes.c_char * QS_TRACE_MAX), ("crossings", ctypes.c_int),
                 ("steps_a", ctypes.c_int), ("steps_b", ctypes.c_int),
                 ("dslash_f32", ctypes.c_int64), ("dslash_f64", ctypes.c_int64),
-                ("cg_iterations", ctypes.c_int64), ("seconds", ctypes.c_double)]
+                ("cg_iterations", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("fail_reason", ctypes.c_int)]
 
     def as_dict(self):
         n = min(self.n, QS_TRACE_MAX)
@@ -66,7 +68,16 @@ class SignReport(ctypes.Structure):
                 "resid": list(self.resid[:n]), "phase": self.phase[:n].decode(),
                 "crossings": self.crossings, "steps_a": self.steps_a, "steps_b": self.steps_b,
                 "dslash_f32": self.dslash_f32, "dslash_f64": self.dslash_f64,
-                "cg_iterations": self.cg_iterations, "seconds": self.seconds}
+                "cg_iterations": self.cg_iterations, "seconds": self.seconds,
+                "fail_reason": self.fail_reason}
+
+
+class KernelProf(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("dslash", KernelProf * 2)]
 
 
 def _load():
@@ -87,6 +98,9 @@ def _load():
         "qs_sign_default_opts": (None, [ctypes.POINTER(SignOpts)]),
         "qs_pfaffian_sign": (I, [P, D, ctypes.POINTER(SignOpts), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(SignReport)]),
+        "qs_set_profiling": (I, [P, I]),
+        "qs_get_profile": (I, [P, ctypes.POINTER(Profile)]),
+        "qs_kernel_launches": (ctypes.c_int64, []),
         "qs_strerror": (ctypes.c_char_p, [I]),
         "qs_last_cuda_error": (ctypes.c_char_p, []),
     }
@@ -198,9 +212,32 @@ def pfaffian_sign(h, m0_target, opts=None):
     o = opts if opts is not None else sign_default_opts()
     sg = ctypes.c_int(0)
     rep = SignReport()
-    _check(_lib.qs_pfaffian_sign(h, float(m0_target), ctypes.byref(o), ctypes.byref(sg), ctypes.byref(rep)),
-           "pfaffian_sign")
+    code = _lib.qs_pfaffian_sign(h, float(m0_target), ctypes.byref(o), ctypes.byref(sg), ctypes.byref(rep))
+    if code != 0:
+        err = QStarError(code, "pfaffian_sign")
+        err.report = rep.as_dict()
+        raise err
     return sg.value, rep.as_dict()
+
+
+def kernel_launches():
+    """qs_kernel_launches: kernels launched by the library so far in this process."""
+    return _lib.qs_kernel_launches()
+
+
+def set_profiling(h, on):
+    _check(_lib.qs_set_profiling(h, int(bool(on))), "set_profiling")
+
+
+def get_profile(h):
+    """{"f64": {...}, "f32": {...}} with launches, ms, bytes of the operator kernels."""
+    p = Profile()
+    _check(_lib.qs_get_profile(h, ctypes.byref(p)), "get_profile")
+    out = {}
+    for name, i in (("f64", QS_F64), ("f32", QS_F32)):
+        k = p.dslash[i]
+        out[name] = {"launches": k.launches, "ms": k.ms, "bytes": k.bytes}
+    return out
 
 
 class Lattice:
@@ -225,6 +262,12 @@ class Lattice:
 
     def pfaffian_sign(self, m0_target, opts=None):
         return pfaffian_sign(self.h, m0_target, opts)
+
+    def set_profiling(self, on):
+        set_profiling(self.h, on)
+
+    def get_profile(self):
+        return get_profile(self.h)
 
     def close(self):
         if self.h is not None:

@@ -329,6 +329,7 @@ cudaError_t qs_norm2(const R *v, int k, int64_t nr, double *part, double *out, c
     dim3 g(QS_RED_BLOCKS, k);
     norm2_part<R><<<g, QS_RED_THREADS, 0, st>>>(v, nr, part);
     finalize_sum<<<k, 256, 0, st>>>(part, QS_RED_BLOCKS, 1, out);
+    qs_note_launches(2);
     return cudaGetLastError();
 }
 template cudaError_t qs_norm2<float>(const float *, int, int64_t, double *, double *, cudaStream_t);
@@ -340,6 +341,7 @@ cudaError_t qs_dot(const R *a, const R *b, int k, int64_t nr, double *part, doub
     dim3 g(QS_RED_BLOCKS, k);
     dot_part<R><<<g, QS_RED_THREADS, 0, st>>>(a, b, nr, part);
     finalize_sum<<<2 * k, 256, 0, st>>>(part, QS_RED_BLOCKS, 1, out);
+    qs_note_launches(2);
     return cudaGetLastError();
 }
 template cudaError_t qs_dot<float>(const float *, const float *, int, int64_t, double *, double *, cudaStream_t);
@@ -351,6 +353,7 @@ cudaError_t qs_resid2(const double *a, const double *b, const double *theta, int
     dim3 g(QS_RED_BLOCKS, k);
     resid_part<<<g, QS_RED_THREADS, 0, st>>>(a, b, theta, nr, part);
     finalize_sum<<<k, 256, 0, st>>>(part, QS_RED_BLOCKS, 1, out);
+    qs_note_launches(2);
     return cudaGetLastError();
 }
 
@@ -369,6 +372,7 @@ cudaError_t qs_gram(const double *A, int ka, const double *B, int kb, int64_t nr
     int nb = (int)(nch < QS_RED_BLOCKS ? nch : QS_RED_BLOCKS);
     gram_part<<<nb, 256, sm, st>>>(A, ka, B, kb, nc, part);
     finalize_sum<<<2 * ka * kb, 256, 0, st>>>(part, nb, 1, reinterpret_cast<double *>(G));
+    qs_note_launches(2);
     return cudaGetLastError();
 }
 
@@ -382,6 +386,7 @@ cudaError_t qs_rotate(const double *W, int ka, const double2 *C, int kc, int64_t
         attr = true;
     }
     rotate_kernel<<<grid_for(nc, 256), 256, sm, st>>>(W, ka, C, kc, nc, V);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -389,6 +394,7 @@ cudaError_t qs_d2f(const double *x, float *y, const double *scale, int k, int64_
 {
     dim3 g(grid_for(nr) / k + 1, k);
     d2f_kernel<<<g, 256, 0, st>>>(x, y, scale, nr);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -396,6 +402,7 @@ cudaError_t qs_axpy_f2d(double *x, const float *e, const double *coef, int k, in
 {
     dim3 g(grid_for(nr) / k + 1, k);
     axpy_f2d_kernel<<<g, 256, 0, st>>>(x, e, coef, nr);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -403,6 +410,7 @@ cudaError_t qs_scale_cols(double *x, const double *scale, int k, int64_t nr, cud
 {
     dim3 g(grid_for(nr) / k + 1, k);
     scale_cols_kernel<<<g, 256, 0, st>>>(x, scale, nr);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -410,6 +418,7 @@ cudaError_t qs_scaled_copy(double *x, const double *b, const double *coef, int k
 {
     dim3 g(grid_for(nr) / k + 1, k);
     scaled_copy_kernel<<<g, 256, 0, st>>>(x, b, coef, nr);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -418,6 +427,7 @@ cudaError_t qs_cheb_step(R *ynew, const R *ay, const R *y, const R *x, double c,
                          int64_t n, cudaStream_t st)
 {
     cheb_kernel<R><<<grid_for(n), 256, 0, st>>>(ynew, ay, y, x, (R)c, (R)s1, (R)s2, n);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 template cudaError_t qs_cheb_step<float>(float *, const float *, const float *, const float *, double, double, double, int64_t, cudaStream_t);
@@ -427,6 +437,7 @@ template <typename R>
 cudaError_t qs_axpby(double a, const R *x, double b, R *y, int64_t n, cudaStream_t st)
 {
     axpby_kernel<R><<<grid_for(n), 256, 0, st>>>((R)a, x, (R)b, y, n);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 template cudaError_t qs_axpby<float>(double, const float *, double, float *, int64_t, cudaStream_t);
@@ -435,12 +446,14 @@ template cudaError_t qs_axpby<double>(double, const double *, double, double *, 
 cudaError_t qs_fill_gauss(double *x, int64_t n, uint64_t seed, cudaStream_t st)
 {
     gauss_kernel<<<grid_for(n), 256, 0, st>>>(x, n, seed);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t qs_map_scalars(const double *in, double *out, int k, int mode, cudaStream_t st)
 {
     map_scalars_kernel<<<1, 64, 0, st>>>(in, out, k, mode);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -449,12 +462,14 @@ cudaError_t qs_cg_update(float *x, float *r, const float *p, const float *ap, Cg
 {
     dim3 g(QS_RED_BLOCKS, k);
     cg_update_kernel<<<g, QS_RED_THREADS, 0, st>>>(x, r, p, ap, s, nr, part);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t qs_cg_finalize(CgScalars s, double tol2, int k, double *part, int *nactive, cudaStream_t st)
 {
     cg_finalize_kernel<<<1, 256, 0, st>>>(s, tol2, k, part, QS_RED_BLOCKS, nactive);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -462,11 +477,13 @@ cudaError_t qs_cg_pupdate(float *p, const float *r, CgScalars s, int k, int64_t 
 {
     dim3 g(grid_for(nr) / k + 1, k);
     cg_p_kernel<<<g, 256, 0, st>>>(p, r, s, nr);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t qs_cg_init(CgScalars s, const double *rr, int k, cudaStream_t st)
 {
     cg_init_kernel<<<1, 64, 0, st>>>(s, rr, k);
+    qs_note_launches(1);
     return cudaGetLastError();
 }

@@ -55,7 +55,12 @@ cudaError_t qs_cg_pupdate(float *p, const float *r, CgScalars s, int k, int64_t 
 cudaError_t qs_cg_init(CgScalars s, const double *rr, int k, cudaStream_t st);
 
 // Ritz values (sorted by |theta|) and residual norms of the current block
+// Ritz pairs ordered by <v, Q^2 v> = theta^2 + r^2; col[i] is the device column of
+// pair i; theta_dev / res_dev are in device column order.
 struct Ritz {
-    double theta[64], res[64], mu[64];
+    double theta[64], res[64];
+    double theta_dev[64], res_dev[64];
+    int col[64];
+    double mu_max;   // largest Q^2 Ritz value of the block
 };
 int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz, int *conv, qs_eig_stats *stats);

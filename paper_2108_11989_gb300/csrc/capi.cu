@@ -5,7 +5,94 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <vector>
+
+// Events around operator launches while profiling is on; resolved in batches.
+struct ProfState {
+    struct Rec {
+        cudaEvent_t a, b;
+        int prec;
+        double bytes;
+    };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    qs_profile acc;
+    int on;
+};
+
+static cudaEvent_t prof_event(ProfState *p)
+{
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static int prof_resolve(qs_lattice *lat)
+{
+    ProfState *p = lat->prof;
+    if (!p || p->pending.empty()) return QS_OK;
+    QS_CUDA(cudaStreamSynchronize(lat->stream));
+    for (auto &r : p->pending) {
+        float ms = 0.f;
+        QS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        qs_kernel_prof &k = p->acc.dslash[r.prec];
+        k.launches += 1;
+        k.ms += ms;
+        k.bytes += r.bytes;
+        p->pool.push_back(r.a);
+        p->pool.push_back(r.b);
+    }
+    p->pending.clear();
+    return QS_OK;
+}
+
+static void prof_free(qs_lattice *lat)
+{
+    ProfState *p = lat->prof;
+    if (!p) return;
+    for (auto &r : p->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : p->pool) cudaEventDestroy(e);
+    delete p;
+    lat->prof = nullptr;
+}
+
+extern "C" int qs_set_profiling(qs_lattice *lat, int on)
+{
+    if (!lat) return QS_EINVAL;
+    QS_CUDA(cudaSetDevice(lat->device));
+    if (on) {
+        if (!lat->prof) lat->prof = new ProfState();
+        QS_TRY(prof_resolve(lat));
+        memset(&lat->prof->acc, 0, sizeof(qs_profile));
+        lat->prof->on = 1;
+    } else if (lat->prof) {
+        lat->prof->on = 0;
+    }
+    return QS_OK;
+}
+
+extern "C" int qs_get_profile(qs_lattice *lat, qs_profile *prof)
+{
+    if (!lat || !prof) return QS_EINVAL;
+    memset(prof, 0, sizeof(*prof));
+    if (!lat->prof) return QS_OK;
+    QS_CUDA(cudaSetDevice(lat->device));
+    QS_TRY(prof_resolve(lat));
+    *prof = lat->prof->acc;
+    return QS_OK;
+}
+
 static char g_last_cuda_error[256] = "";
+static long long g_launches = 0;
+
+void qs_note_launches(int n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
+
+extern "C" int64_t qs_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 void qs_record_cuda_error(cudaError_t e, const char *where)
 {
@@ -58,6 +145,7 @@ extern "C" int qs_destroy_lattice(qs_lattice *lat)
     cudaSetDevice(lat->device);
     qs_free_gauge(lat);
     qs_free_workspace(lat);
+    prof_free(lat);
     free(lat);
     return QS_OK;
 }
@@ -120,7 +208,21 @@ static int run_typed(qs_lattice *lat, int pi, const double *m0, const void *in, 
             tv = bv + 1;
         }
     }
+    ProfState *pf = (lat->prof && lat->prof->on) ? lat->prof : nullptr;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    if (pf) {
+        if (pf->pending.size() >= 4096) QS_TRY(prof_resolve(lat));
+        ea = prof_event(pf);
+        eb = prof_event(pf);
+        QS_CUDA(cudaEventRecord(ea, lat->stream));
+    }
     cudaError_t e = qs_dslash_launch<R>(d, nrhs, tv - 1, lat->stream);
+    qs_note_launches(1);
+    if (pf) {
+        QS_CUDA(cudaEventRecord(eb, lat->stream));
+        pf->pending.push_back({ea, eb, pi == 0 ? QS_F64 : QS_F32,
+                               (double)lat->g.Ns * (48.0 * nrhs + 72.0) * sizeof(R)});
+    }
     if (e != cudaSuccess) {
         qs_record_cuda_error(e, "dslash launch");
         return QS_ECUDA;

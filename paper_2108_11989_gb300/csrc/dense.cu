@@ -172,6 +172,7 @@ cudaError_t qs_chol_rinv(const double2 *G, int k, double2 *Rinv, int *info, cuda
 {
     if (k > 64) return cudaErrorInvalidValue;
     chol_rinv_kernel<<<1, 64, k * k * sizeof(double2), st>>>(G, k, Rinv, info);
+    qs_note_launches(1);
     return cudaGetLastError();
 }
 
@@ -184,5 +185,6 @@ cudaError_t qs_herm_eig(const double2 *H, int k, double *evals, double2 *Y, int 
         attr = true;
     }
     jacobi_kernel<<<1, 64, 2 * k * k * sizeof(double2), st>>>(H, k, evals, Y, info);
+    qs_note_launches(1);
     return cudaGetLastError();
 }

@@ -54,6 +54,8 @@ struct qs_lattice {
     int tuned[2][65];
     // solver workspace (allocated on first use, see solver.cu)
     struct Workspace *ws;
+    // kernel profiling state (capi.cu), NULL when off
+    struct ProfState *prof;
 };
 
 // neighbour of doubled site s in direction mu, step +1/-1; *sgn = fermion bc factor
@@ -140,3 +142,6 @@ template <typename R> __host__ __device__ inline C2<R> cj_mul(C2<R> a, C2<R> b)
 __host__ __device__ inline int qs_tri(int i, int j) { return i * (i - 1) / 2 + j; }
 
 Geom qs_make_geom(int L, int T, int cstar_mask, int t_anti);
+
+// process-wide count of kernel launches made by the library
+void qs_note_launches(int n);

@@ -5,7 +5,9 @@
 // Step A follows the enumerated algorithm of Sec. 3: m_{n+1} = m_n + c lambda_bar_n;
 // stop for step B when lambda_bar decreases, stop with the sign once m > m0_max.
 // The no-crossing certificate of eq. derivativebound (|lambda'| <= 1) is checked
-// with lower bounds: (lb_n - r_n) + (lb_{n+1} - r_{n+1}) >= m_{n+1} - m_n.
+// with lower bounds: (lb_n - r_n) + (lb_{n+1} - r_{n+1}) >= m_{n+1} - m_n; a step
+// that fails it is shortened to m_n + 0.95 (lb_n - r_n), the edge of the interval
+// around m_n that is free of crossings.
 //
 // Step B (our reading; the paper defers to other work): at mass m with tracked
 // window |theta_0| <= ... (all with residual bounds), pick the widest gap between
@@ -38,6 +40,7 @@ extern "C" void qs_sign_default_opts(qs_sign_opts *o)
 namespace {
 
 struct Flow {
+    int nb;            // step-B prefix size (values that must converge)
     qs_lattice *lat;
     qs_sign_opts o;
     qs_sign_report *rep;
@@ -55,16 +58,21 @@ double now_s()
 int modes(Flow &f, double m, char phase, Ritz *rz)
 {
     qs_eig_opts e = f.o.eig;
-    e.warm_start = 1;
-    // step B reads the whole window, but only through residual bounds: the gap it
-    // steps in lies between bounds s_i + r_i and s_{i+1} - r_{i+1}, so Ritz values far
-    // from convergence just make that gap narrower; only the leading ones must converge
-    if (phase == 'B' && e.nwant < 4) e.nwant = 4 < e.k - 2 ? 4 : e.k - 2;
+    // the first mass starts as the caller asks (cold or from the handle's last
+    // subspace); every later mass starts from the previous one
+    if (f.rep->n > 0) e.warm_start = 1;
+    // step B converges a prefix of k/2 Ritz values; the rest of the block are guard
+    // vectors whose Ritz values enter only through their residual bounds
+    if (phase == 'B') {
+        e.nwant = std::max(e.nwant, f.nb);
+        // the counts only need bounds that separate at the gap
+        e.tol = std::max(e.tol, 1e-4);
+    }
     int conv = 0;
     qs_eig_stats st;
     memset(&st, 0, sizeof(st));
     int s = qs_lowmodes_impl(f.lat, m, &e, rz, &conv, &st);
-    if (s != QS_OK) return s;
+    if (s != QS_OK) { f.rep->fail_reason = 1; return s; }
     qs_sign_report *r = f.rep;
     r->dslash_f32 += st.dslash_f32;
     r->dslash_f64 += st.dslash_f64;
@@ -77,6 +85,7 @@ int modes(Flow &f, double m, char phase, Ritz *rz)
     }
     r->n++;
     if (phase == 'A') r->steps_a++; else r->steps_b++;
+    if (!conv) r->fail_reason = 1;
     return conv ? QS_OK : QS_ENOCONV;
 }
 
@@ -96,9 +105,9 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
     if (!(f.o.c > 0 && f.o.c < 2) || f.o.eig.k < 4 || f.o.max_steps < 1) return QS_EINVAL;
     f.rep = rep;
     f.steps = 0;
+    f.nb = 2;
     f.t0 = now_s();
     const double m0max = f.o.m0_max > 0 ? f.o.m0_max : 3.0 * (lat->csw_su3 + lat->csw_u1);
-    const int kw = f.o.eig.k - 2;   // tracked window in step B
     int st;
     auto finish = [&](int status) {
         rep->seconds = now_s() - f.t0;
@@ -106,68 +115,137 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
     };
 
     double m = m_target;
-    Ritz cur, prev_r;
+    Ritz cur;
     st = modes(f, m, 'A', &cur);
     if (st != QS_OK) return finish(st);
     if (fabs(cur.theta[0]) - cur.res[0] <= 0) return finish(QS_EUNDECIDED);
     long flips = 0;
     while (f.steps < f.o.max_steps) {
         // ---- step A -------------------------------------------------------------
-        int n = 0;
         bool go_b = false;
-        double pm = m, plb = 0, prb = 0;
         while (f.steps < f.o.max_steps) {
             double lb = fabs(cur.theta[0]), rb = cur.res[0];
-            if (n >= 1) {
-                bool covered = (plb - prb) + (lb - rb) >= (m - pm);
-                if (lb < plb || !covered) {          // step 3, or the certificate fails
-                    go_b = true;
-                    if (!covered) { m = pm; cur = prev_r; }
-                    break;
-                }
-            }
+            if (!(lb - rb > 0)) { rep->fail_reason = 6; return finish(QS_EUNDECIDED); }
             // step 4; also stop once the no-crossing interval (m - lb, m + lb) of
             // eq. derivativebound already reaches past m0_max
             if (m > m0max || m + (lb - rb) > m0max) {
                 *sign = (flips % 2 == 0) ? 1 : -1;
                 return finish(QS_OK);
             }
-            pm = m; prev_r = cur; plb = lb; prb = rb;
-            m = m + f.o.c * lb;                      // step 5
-            st = modes(f, m, 'A', &cur);
+            double mn = m + f.o.c * lb;              // step 5
+            Ritz nw;
+            st = modes(f, mn, 'A', &nw);
             if (st != QS_OK) return finish(st);
-            ++n;
             ++f.steps;
+            double lb2 = fabs(nw.theta[0]), rb2 = nw.res[0];
+            if ((lb - rb) + (lb2 - rb2) < (mn - m)) {
+                // the step left part of [m, mn] outside both crossing-free intervals:
+                // retreat to the edge of the one around m
+                mn = m + 0.95 * (lb - rb);
+                st = modes(f, mn, 'A', &nw);
+                if (st != QS_OK) return finish(st);
+                ++f.steps;
+                lb2 = fabs(nw.theta[0]);
+            }
+            m = mn;
+            cur = nw;
+            if (lb2 < lb) { go_b = true; break; }   // step 3: lambda_bar decreases
         }
         if (!go_b) break;
         // ---- step B -------------------------------------------------------------
+        // The window is the whole block; every Ritz value t_i stands for an
+        // eigenvalue in [t_i - r_i, t_i + r_i].  The step dm is taken inside a gap
+        // (a - g, a + g) of the |lambda| bounds, g >= dm: either between two values of
+        // the converged prefix (sorted by |theta|) or above the prefix, below the lower
+        // bounds of all other Ritz values.  Then no eigenvalue crosses |lambda| = a in
+        // the step (|lambda'| <= 1), and the change of N_- is the change of the number
+        // of values certainly in (-a, 0).  A value whose bounds straddle a at the new
+        // mass leaves the step uncertified (QS_ENOCONV).  Values are counted over the
+        // converged prefix (ended at a gap of the window); for the gap above it the guard
+        // values beyond it must lie certainly above a at both masses.
+        const int kk = f.o.eig.k;
+        // prefix size: end the prefix at the widest relative gap of the window, among
+        // sizes 2 .. 3k/4, so it never cuts into a cluster
+        auto pick_prefix = [&](const Ritz &rz) {
+            // q_i = sqrt(theta_i^2 + r_i^2) = ||Q v_i||, the order the window is kept in:
+            // close to |lambda| for converged values, large for unconverged ones
+            int best_n = std::max(2, f.o.eig.nwant);
+            double best_g = -1e300;
+            for (int n = std::max(2, f.o.eig.nwant); n <= (3 * kk) / 4; n += 2) {
+                double qa = hypot(rz.theta[n - 1], rz.res[n - 1]), qb = hypot(rz.theta[n], rz.res[n]);
+                double g = (qb - qa) / (qb + 1e-300);
+                if (g > best_g) { best_g = g; best_n = n; }
+            }
+            return best_n;
+        };
+        f.nb = pick_prefix(cur);
+        int nb = f.nb;
+        // the window at the start mass was solved for step A (few values converged):
+        // solve it again (warm) for the step-B prefix
+        st = modes(f, m, 'B', &cur);
+        if (st != QS_OK) return finish(st);
         while (f.steps < f.o.max_steps) {
-            double s[64], r[64];
-            for (int i = 0; i < kw; ++i) { s[i] = fabs(cur.theta[i]); r[i] = cur.res[i]; }
-            double best = -1;
-            int bi = -1;
-            for (int i = 0; i + 1 < kw; ++i) {
-                double g = (s[i + 1] - r[i + 1]) - (s[i] + r[i]);
-                if (g > best) { best = g; bi = i; }
+            int idx[64];
+            for (int i = 0; i < nb; ++i) idx[i] = i;
+            std::sort(idx, idx + nb, [&](int x, int y) { return fabs(cur.theta[x]) < fabs(cur.theta[y]); });
+            // lowest lower bound among the guard values (the block beyond the prefix);
+            // guards with r > |theta| / 2 are unconverged mixtures that say nothing about
+            // where the next eigenvalue lies and are skipped
+            auto guard_low = [&](const Ritz &rz) {
+                double lo = 1e300;
+                int any = 0;
+                for (int j = nb; j < kk; ++j)
+                    if (rz.res[j] <= 0.5 * fabs(rz.theta[j])) { lo = std::min(lo, fabs(rz.theta[j]) - rz.res[j]); any = 1; }
+                return any ? lo : -1e300;
+            };
+            double guard_lo = guard_low(cur);
+            double best = -1, a = 0;
+            int above_gap = 0;
+            // inner gaps: a prefix value above a already bounds (block containing the
+            // lowest eigenvalues) every eigenvalue outside the prefix from below
+            for (int q = 0; q + 1 < nb; ++q) {
+                int i = idx[q], j = idx[q + 1];
+                double lo = fabs(cur.theta[i]) + cur.res[i], hi = fabs(cur.theta[j]) - cur.res[j];
+                if (hi - lo > best) { best = hi - lo; a = 0.5 * (lo + hi); above_gap = 0; }
+            }
+            // the gap above the prefix needs the guard values' lower bounds
+            {
+                double lo = fabs(cur.theta[idx[nb - 1]]) + cur.res[idx[nb - 1]];
+                if (guard_lo - lo > best) { best = guard_lo - lo; a = 0.5 * (lo + guard_lo); above_gap = 1; }
             }
             double dm = 0.5 * best * 0.95;
-            if (bi < 0 || !(dm > 1e-13)) return finish(QS_ENOCONV);
-            double a = 0.5 * ((s[bi] + r[bi]) + (s[bi + 1] - r[bi + 1]));
-            int before = 0;
-            for (int i = 0; i < kw; ++i) before += (cur.theta[i] < 0 && fabs(cur.theta[i]) < a);
-            double lb_old = s[0];
+            if (!(dm > 1e-13)) { rep->fail_reason = 2; return finish(QS_ENOCONV); }
+            // count over the converged prefix.  *ok: for an inner gap some prefix value
+            // lies certainly above a; for the gap above the prefix every guard value does
+            auto count_below = [&](const Ritz &rz, int *neg, int *straddle, int *ok) {
+                *neg = 0; *straddle = 0;
+                int pre_above = 0, guards_above = 1;
+                for (int i = 0; i < nb; ++i) {
+                    double t = fabs(rz.theta[i]), r = rz.res[i];
+                    if (t + r < a) *neg += rz.theta[i] < 0;
+                    else if (t - r <= a) ++*straddle;
+                    else pre_above = 1;
+                }
+                if (!(guard_low(rz) > a)) guards_above = 0;
+                *ok = above_gap ? guards_above : pre_above;
+            };
+            int before, sb, ab, after, sa, aa;
+            count_below(cur, &before, &sb, &ab);
+            double lb_old = fabs(cur.theta[0]);
             m += dm;
             st = modes(f, m, 'B', &cur);
             if (st != QS_OK) return finish(st);
             ++f.steps;
-            int after = 0;
-            for (int i = 0; i < kw; ++i) after += (cur.theta[i] < 0 && fabs(cur.theta[i]) < a);
+            count_below(cur, &after, &sa, &aa);
+            if (sb || sa || !ab || !aa) { rep->fail_reason = 3; return finish(QS_ENOCONV); }
             int d = after - before;
-            if (d % 2) return finish(QS_ENUMERIC);   // the degenerate pairs must stay paired
+            if (d % 2) { rep->fail_reason = 4; return finish(QS_ENUMERIC); }   // pairs must stay paired
             flips += d / 2;
             rep->crossings += abs(d) / 2;
             if (fabs(cur.theta[0]) > lb_old) break;  // lambda_bar grows again: step A
+            f.nb = nb = pick_prefix(cur);
         }
     }
+    rep->fail_reason = 5;
     return finish(QS_ENOCONV);
 }

@@ -136,56 +136,57 @@ static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp,
     return QS_OK;
 }
 
-// Rayleigh-Ritz on the orthonormal block V = blk64[0], in two stages.
-// (1) Q^2 stage: H2 = (QV)^H (QV), V <- V Y ordered by the Q^2 Ritz values mu.  The
-//     wanted |lambda| are the lowest of Q^2, an end of its spectrum, so this stage
-//     has no spurious Ritz values (a Rayleigh-Ritz with the indefinite Q can pair
-//     +lambda and -lambda contaminations into a small, meaningless theta).
-// (2) Q stage on the leading kc = k - 2 columns: signed Ritz values theta of Q,
-//     sorted by |theta|; the last two columns keep theta = <v, Q v>.
-// Afterwards blk64[0] = V, blk64[1] = Q V; theta, residuals ||Q v - theta v|| and
-// mu are on the host.
-static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *rz)
+// Rayleigh-Ritz on the orthonormal block V = blk64[0].
+// * mu: Ritz values of Q^2 (H2 = (QV)^H QV); only the largest is used, as the lower
+//   edge of the next filter interval.
+// * theta: Ritz values of Q over the whole block (H = V^H Q V), V <- V Y, QV <- QV Y,
+//   residuals r = ||Q v - theta v|| (some eigenvalue of Q lies within r of theta).
+// The low |lambda| of the indefinite Q are interior eigenvalues, where Ritz values can
+// be spurious (+lambda and -lambda contaminations averaging to a small theta, with a
+// large r).  The pairs are therefore ordered by <v, Q^2 v> = theta^2 + r^2, which is
+// close to lambda^2 for a genuine pair and large for a spurious one.
+// prec: operator precision (FP32 while far from convergence, FP64 otherwise).
+static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *rz, int prec)
 {
     cudaStream_t st = lat->stream;
-    const int kc = k - 2;
-    const size_t colb = (size_t)w->nr * sizeof(double);
-    QS_TRY(opQ(lat, w, QS_F64, m0, w->blk64[0], w->blk64[1], k));
-    // (1) Q^2 stage
+    if (prec == QS_F64) {
+        QS_TRY(opQ(lat, w, QS_F64, m0, w->blk64[0], w->blk64[1], k));
+    } else {
+        CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
+        QS_TRY(opQ(lat, w, QS_F32, m0, w->blk32[0], w->blk32[1], k));
+        CK(cudaMemsetAsync(w->blk64[1], 0, (size_t)k * w->nr * sizeof(double), st));
+        CK(qs_axpy_f2d(w->blk64[1], w->blk32[1], DS(w, S_ONES), k, w->nr, st));
+    }
     CK(qs_gram(w->blk64[1], k, w->blk64[1], k, w->nr, w->part, w->Hm, st));
-    CK(qs_herm_eig(w->Hm, k, DS(w, S_TMP), w->Ym, w->di + 66, st));
+    CK(qs_herm_eig(w->Hm, k, DS(w, S_RN), w->Ym, w->di + 66, st));
+    CK(qs_gram(w->blk64[0], k, w->blk64[1], k, w->nr, w->part, w->Hm, st));
+    CK(qs_herm_eig(w->Hm, k, DS(w, S_THETA), w->Ym, w->di + 67, st));
     CK(qs_rotate(w->blk64[0], k, w->Ym, k, w->nr, w->blk64[2], st));
     CK(qs_rotate(w->blk64[1], k, w->Ym, k, w->nr, w->blk64[3], st));
     std::swap(w->blk64[0], w->blk64[2]);
     std::swap(w->blk64[1], w->blk64[3]);
-    CK(cudaMemcpyAsync(rz->mu, DS(w, S_TMP), k * sizeof(double), cudaMemcpyDeviceToHost, st));
-    // (2) Q stage on the leading kc columns
-    CK(qs_gram(w->blk64[0], kc, w->blk64[1], kc, w->nr, w->part, w->Hm, st));
-    CK(qs_herm_eig(w->Hm, kc, DS(w, S_THETA), w->Ym, w->di + 67, st));
-    CK(qs_rotate(w->blk64[0], kc, w->Ym, kc, w->nr, w->blk64[2], st));
-    CK(qs_rotate(w->blk64[1], kc, w->Ym, kc, w->nr, w->blk64[3], st));
-    CK(cudaMemcpyAsync(w->blk64[2] + (size_t)kc * w->nr, w->blk64[0] + (size_t)kc * w->nr, (k - kc) * colb,
-                       cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(w->blk64[3] + (size_t)kc * w->nr, w->blk64[1] + (size_t)kc * w->nr, (k - kc) * colb,
-                       cudaMemcpyDeviceToDevice, st));
-    std::swap(w->blk64[0], w->blk64[2]);
-    std::swap(w->blk64[1], w->blk64[3]);
-    // theta of the trailing columns: <v, Q v>
-    CK(qs_dot<double>(w->blk64[0] + (size_t)kc * w->nr, w->blk64[1] + (size_t)kc * w->nr, k - kc, w->nr,
-                      w->part, DS(w, S_COEF), st));
-    QS_TRY(sync_read(lat, w, S_COEF, 2 * (k - kc)));
-    for (int i = kc; i < k; ++i) w->hp[64 * S_TMP + i] = w->hp[64 * S_COEF + 2 * (i - kc)];
-    CK(cudaMemcpyAsync(DS(w, S_THETA) + kc, w->hp + 64 * S_TMP + kc, (k - kc) * sizeof(double),
-                       cudaMemcpyHostToDevice, st));
     CK(qs_resid2(w->blk64[1], w->blk64[0], DS(w, S_THETA), k, w->nr, w->part, DS(w, S_TMP), st));
     CK(cudaMemcpyAsync(w->hp + 64 * S_THETA, DS(w, S_THETA), k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w->hp + 64 * S_RN, DS(w, S_RN), k * sizeof(double), cudaMemcpyDeviceToHost, st));
     QS_TRY(sync_read(lat, w, S_TMP, k));
     if (w->hi[64] || w->hi[65]) return QS_ENUMERIC;   // Cholesky-QR broke down
+    double th[64], rs[64], key[64];
+    rz->mu_max = 0;
     for (int i = 0; i < k; ++i) {
-        rz->theta[i] = w->hp[64 * S_THETA + i];
+        th[i] = w->hp[64 * S_THETA + i];
         double r2 = w->hp[64 * S_TMP + i];
-        rz->res[i] = sqrt(r2 > 0 ? r2 : 0);
-        if (!isfinite(rz->theta[i]) || !isfinite(rz->res[i])) return QS_ENUMERIC;
+        rs[i] = sqrt(r2 > 0 ? r2 : 0);
+        key[i] = th[i] * th[i] + rs[i] * rs[i];
+        rz->mu_max = std::max(rz->mu_max, fabs(w->hp[64 * S_RN + i]));
+        rz->theta_dev[i] = th[i];
+        rz->res_dev[i] = rs[i];
+        rz->col[i] = i;
+        if (!isfinite(th[i]) || !isfinite(rs[i])) return QS_ENUMERIC;
+    }
+    std::stable_sort(rz->col, rz->col + k, [&](int a, int b) { return key[a] < key[b]; });
+    for (int i = 0; i < k; ++i) {
+        rz->theta[i] = th[rz->col[i]];
+        rz->res[i] = rs[rz->col[i]];
     }
     return QS_OK;
 }
@@ -317,7 +318,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
     }
     w->have_V = 0;
     QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k));
-    QS_TRY(rayleigh_ritz(lat, w, m0, k, rz));
+    QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F32));
     // b >= lambda_max(Q^2): ||Q|| = ||D|| <= max_x ||4 + m0 + A(x)|| + ||hopping||,
     // ||hopping|| <= 4 (each direction is a partial isometry pair of norm 1)
     double qn = fabs(4.0 + m0) + lat->clov_norm + 4.0;
@@ -325,7 +326,8 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
     int it = 0, nf = 0, nref = 0;
     *conv = 0;
     double prev_worst = 1e300;
-    int stall = 0, fstall = 0;
+    int stall = 0, fstall = 0, restarts = 0;
+    int last_prec = QS_F32;
     for (it = 0; it < o->max_iter; ++it) {
         double worst = 0;
         for (int i = 0; i < o->nwant; ++i)
@@ -335,14 +337,45 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         // depend on how small lambda_bar is.  The FP32 filter cannot improve a block
         // below ~1e-5 relative residual, so only a stagnating refinement hands back.
         bool refine = (worst < 1e-3 || fstall >= 2) && !(stall >= 3 && worst > 1e-5);
+        if (stall >= 3 && fstall >= 2 && restarts < 3) {
+            // both stages stagnate (typically a warm start from a distant mass): keep the
+            // converged pairs, moved to the front so Cholesky-QR preserves them, and
+            // refill the rest of the block with random vectors
+            int nconv = 0;
+            double2 P[64 * 64];
+            for (int i = 0; i < k * k; ++i) P[i] = make_double2(0, 0);
+            for (int i = 0; i < k; ++i)
+                if (rz->res[i] <= o->tol * fabs(rz->theta[i])) P[rz->col[i] * k + nconv++] = make_double2(1, 0);
+            for (int i = 0, j = nconv; i < k; ++i)
+                if (!(rz->res[i] <= o->tol * fabs(rz->theta[i]))) P[rz->col[i] * k + j++] = make_double2(1, 0);
+            CK(cudaMemcpyAsync(w->Ym, P, k * k * sizeof(double2), cudaMemcpyHostToDevice, st));
+            CK(qs_rotate(w->blk64[0], k, w->Ym, k, w->nr, w->blk64[2], st));
+            std::swap(w->blk64[0], w->blk64[2]);
+            CK(qs_fill_gauss(w->blk64[0] + (size_t)nconv * w->nr, (int64_t)(k - nconv) * w->nr,
+                             o->seed * 0x2545F4914F6CDD1DULL + 977 * (restarts + 1), st));
+            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k));
+            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F32));
+            last_prec = QS_F32;
+            stall = fstall = 0;
+            prev_worst = 1e300;
+            ++restarts;
+            if (verbose()) fprintf(stderr, "[qstar] m0=%.6f restart keeping %d converged pairs\n", m0, nconv);
+            continue;
+        }
         if (verbose())
             fprintf(stderr, "[qstar] m0=%.6f pass %d worst_rel_res=%.3e theta0=%.6e res0=%.3e theta_k=%.4e b=%.3e next=%s\n",
                     m0, it, worst, rz->theta[0], rz->res[0], rz->theta[k - 1], b,
                     worst <= o->tol ? "done" : (refine ? "refine" : "filter"));
-        if (worst <= o->tol) { *conv = 1; break; }
+        if (worst <= o->tol) {
+            if (last_prec == QS_F64) { *conv = 1; break; }
+            // confirm with the FP64 operator before accepting
+            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F64));
+            last_prec = QS_F64;
+            continue;
+        }
         if (!refine) {
             // Chebyshev filter on [a, b], a = largest Q^2 Ritz value of the block
-            double a = rz->mu[k - 1];
+            double a = rz->mu_max;
             if (a >= 0.5 * b || it == 0) a = std::min(a, 0.05 * b);
             CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
             float *Y = nullptr;
@@ -355,8 +388,8 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             // power step with Q^-2: X = Q^-2 V, started from V_i / <v_i, Q^2 v_i>
             // (<v, Q^2 v> = theta^2 + r^2 for each Ritz vector)
             double inv[64];
-            for (int i = 0; i < k; ++i) {
-                double q2 = rz->theta[i] * rz->theta[i] + rz->res[i] * rz->res[i];
+            for (int i = 0; i < k; ++i) {   // device column order
+                double q2 = rz->theta_dev[i] * rz->theta_dev[i] + rz->res_dev[i] * rz->res_dev[i];
                 inv[i] = q2 > 0 ? 1.0 / q2 : 0.0;
             }
             CK(cudaMemcpyAsync(DS(w, S_COEF), inv, k * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -369,12 +402,15 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             ++nref;
         }
         QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k));
-        QS_TRY(rayleigh_ritz(lat, w, m0, k, rz));
+        // FP32 operator while the block is far from converged (its residuals are then
+        // far above FP32 rounding); FP64 from the refinement stage on
+        last_prec = (refine || worst < 1e-3) ? QS_F64 : QS_F32;
+        QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, last_prec));
         double nw = 0;
         for (int i = 0; i < o->nwant; ++i)
             nw = std::max(nw, rz->res[i] / std::max(fabs(rz->theta[i]), 1e-300));
-        if (refine && nw > 0.97 * prev_worst) ++stall; else stall = 0;
-        if (!refine && nw > 0.9 * prev_worst) ++fstall; else if (!refine) fstall = 0;
+        if (refine) { if (nw > 0.97 * prev_worst) ++stall; else stall = 0; }
+        else { if (nw > 0.9 * prev_worst) ++fstall; else fstall = 0; }
         prev_worst = nw;
     }
     w->have_V = 1;
@@ -406,9 +442,11 @@ extern "C" int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts
     int conv = 0;
     QS_TRY(qs_lowmodes_impl(lat, m0, &o, &rz, &conv, stats));
     for (int i = 0; i < o.k; ++i) { evals[i] = rz.theta[i]; resid[i] = rz.res[i]; }
-    if (evecs) {
-        CK(cudaMemcpyAsync(evecs, lat->ws->blk64[0], (size_t)o.k * lat->ws->nr * sizeof(double),
-                           cudaMemcpyDeviceToDevice, lat->stream));
+    if (evecs) {   // Ritz vectors in the order of the returned values
+        const size_t colb = (size_t)lat->ws->nr * sizeof(double);
+        for (int i = 0; i < o.k; ++i)
+            CK(cudaMemcpyAsync((char *)evecs + i * colb, lat->ws->blk64[0] + (size_t)rz.col[i] * lat->ws->nr,
+                               colb, cudaMemcpyDeviceToDevice, lat->stream));
         CK(cudaStreamSynchronize(lat->stream));
     }
     return conv ? QS_OK : QS_ENOCONV;
