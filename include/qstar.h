@@ -215,6 +215,27 @@ QS_API int qs_get_profile(qs_lattice *lat, qs_profile *prof);
 /* Number of CUDA kernels this library has launched in this process (all handles). */
 QS_API int64_t qs_kernel_launches(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free operator application (the paper has no counterpart: this is
+ * for callers that cannot allocate device memory when they apply the operator,
+ * such as code running while a CUDA graph is captured, host callbacks, or
+ * frameworks that own every allocation).
+ *
+ * out = Q(m0) in (as qs_apply_Q) and norm2[r] = ||out_r||^2 for r < nrhs.
+ * in, out: DEVICE buffers as for qs_apply_Q; norm2: DEVICE array of nrhs doubles.
+ * nrhs must be <= 64: the norm reduction keeps its partial sums in one static
+ * device array of 608 x 64 doubles (311 KB, held by every device that loads the
+ * library until the process exits); larger nrhs returns QS_EINVAL.  The call
+ * allocates nothing (no cudaMalloc, no events; the operator uses the variant the
+ * handle's autotuner chose earlier, else a fixed one).  Its first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current: make that first call before any stream capture.  Every call shares the
+ * array, so calls whose work overlaps on the GPU (other streams, other handles of
+ * the same device) race; calls on one stream are ordered and safe.  Asynchronous
+ * on the handle's stream. */
+QS_API int qs_apply_Q_norm2_noalloc(qs_lattice *lat, double m0, const void *in, void *out, int nrhs,
+                                    int prec, double *norm2);
+
 /* Static description of a status code. */
 QS_API const char *qs_strerror(int status);
 

@@ -101,6 +101,7 @@ def _load():
         "qs_set_profiling": (I, [P, I]),
         "qs_get_profile": (I, [P, ctypes.POINTER(Profile)]),
         "qs_kernel_launches": (ctypes.c_int64, []),
+        "qs_apply_Q_norm2_noalloc": (I, [P, D, P, P, I, I, P]),
         "qs_strerror": (ctypes.c_char_p, [I]),
         "qs_last_cuda_error": (ctypes.c_char_p, []),
     }
@@ -218,6 +219,13 @@ def pfaffian_sign(h, m0_target, opts=None):
         err.report = rep.as_dict()
         raise err
     return sg.value, rep.as_dict()
+
+
+def apply_Q_norm2_noalloc(h, m0, inp, out, norm2):
+    """qs_apply_Q_norm2_noalloc: out = Q in and norm2[r] = |out_r|^2 (device tensors),
+    with no device allocation by the library."""
+    _check(_lib.qs_apply_Q_norm2_noalloc(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
+                                         _prec_of(inp), norm2.data_ptr()), "apply_Q_norm2_noalloc")
 
 
 def kernel_launches():
