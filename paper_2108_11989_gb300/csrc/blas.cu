@@ -3,6 +3,8 @@
 // vector, then one fixed-order pass), so results are bit-reproducible.
 #include "blas.cuh"
 
+#include <type_traits>
+
 namespace {
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -89,6 +91,9 @@ __global__ void resid_part(const double *__restrict__ a, const double *__restric
 // elements staged in shared memory; pair q = i * kb + j, thread owns q = tid + 256 m.
 #define GCH 32
 #define GMAXP 16
+// LOWP: products and the sum over one chunk of GCH elements in FP32, chunk sums
+// accumulated in FP64 (one FP64 add per chunk instead of four FMAs per element)
+template <bool LOWP>
 __global__ void __launch_bounds__(256) gram_part(const double *__restrict__ A, int ka,
                                                  const double *__restrict__ B, int kb, int64_t nc,
                                                  double *part)
@@ -120,14 +125,26 @@ __global__ void __launch_bounds__(256) gram_part(const double *__restrict__ A, i
             if (q < P) {
                 int i = q / kb, j = q % kb;
                 const double2 *x = sa + i * GCH, *y = sb + j * GCH;
-                double re = ar[m], im = ai[m];
+                if (LOWP) {
+                    float re = 0.f, im = 0.f;
 #pragma unroll 8
-                for (int e = 0; e < GCH; ++e) {
-                    double2 u = x[e], w = y[e];
-                    re = fma(u.x, w.x, fma(u.y, w.y, re));
-                    im = fma(u.x, w.y, fma(-u.y, w.x, im));
+                    for (int e = 0; e < GCH; ++e) {
+                        double2 u = x[e], w = y[e];
+                        float ux = (float)u.x, uy = (float)u.y, wx = (float)w.x, wy = (float)w.y;
+                        re = fmaf(ux, wx, fmaf(uy, wy, re));
+                        im = fmaf(ux, wy, fmaf(-uy, wx, im));
+                    }
+                    ar[m] += re; ai[m] += im;
+                } else {
+                    double re = ar[m], im = ai[m];
+#pragma unroll 8
+                    for (int e = 0; e < GCH; ++e) {
+                        double2 u = x[e], w = y[e];
+                        re = fma(u.x, w.x, fma(u.y, w.y, re));
+                        im = fma(u.x, w.y, fma(-u.y, w.x, im));
+                    }
+                    ar[m] = re; ai[m] = im;
                 }
-                ar[m] = re; ai[m] = im;
             }
         }
     }
@@ -141,6 +158,8 @@ __global__ void __launch_bounds__(256) gram_part(const double *__restrict__ A, i
     }
 }
 
+// LOWP: the k-term sums in FP32 (inputs rounded to FP32), stored as FP64
+template <bool LOWP>
 __global__ void rotate_kernel(const double *__restrict__ W, int ka, const double2 *__restrict__ C, int kc,
                               int64_t nc, double *__restrict__ V)
 {
@@ -151,23 +170,26 @@ __global__ void rotate_kernel(const double *__restrict__ W, int ka, const double
     double2 *V2 = reinterpret_cast<double2 *>(V);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
         for (int j0 = 0; j0 < kc; j0 += 8) {
-            double re[8], im[8];
+            typedef typename std::conditional<LOWP, float, double>::type T;
+            T re[8], im[8];
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) { re[jj] = 0; im[jj] = 0; }
             for (int i = 0; i < ka; ++i) {
                 double2 w = W2[(int64_t)i * nc + e];
+                T wx = (T)w.x, wy = (T)w.y;
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
                     if (j0 + jj < kc) {
                         double2 c = csh[i * kc + j0 + jj];
-                        re[jj] = fma(w.x, c.x, fma(-w.y, c.y, re[jj]));
-                        im[jj] = fma(w.x, c.y, fma(w.y, c.x, im[jj]));
+                        T cx = (T)c.x, cy = (T)c.y;
+                        re[jj] = wx * cx - wy * cy + re[jj];
+                        im[jj] = wx * cy + wy * cx + im[jj];
                     }
                 }
             }
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj)
-                if (j0 + jj < kc) V2[(int64_t)(j0 + jj) * nc + e] = make_double2(re[jj], im[jj]);
+                if (j0 + jj < kc) V2[(int64_t)(j0 + jj) * nc + e] = make_double2((double)re[jj], (double)im[jj]);
         }
     }
 }
@@ -358,34 +380,39 @@ cudaError_t qs_resid2(const double *a, const double *b, const double *theta, int
 }
 
 cudaError_t qs_gram(const double *A, int ka, const double *B, int kb, int64_t nr, double *part,
-                    double2 *G, cudaStream_t st)
+                    double2 *G, cudaStream_t st, int lowp)
 {
     if (ka * kb > 256 * GMAXP) return cudaErrorInvalidValue;
     int64_t nc = nr / 2;
     size_t sm = (size_t)(ka + kb) * GCH * sizeof(double2);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(gram_part, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * GCH * 16);
+        cudaFuncSetAttribute(gram_part<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * GCH * 16);
+        cudaFuncSetAttribute(gram_part<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * GCH * 16);
         attr = true;
     }
     int64_t nch = (nc + GCH - 1) / GCH;
     int nb = (int)(nch < QS_RED_BLOCKS ? nch : QS_RED_BLOCKS);
-    gram_part<<<nb, 256, sm, st>>>(A, ka, B, kb, nc, part);
+    if (lowp) gram_part<true><<<nb, 256, sm, st>>>(A, ka, B, kb, nc, part);
+    else gram_part<false><<<nb, 256, sm, st>>>(A, ka, B, kb, nc, part);
     finalize_sum<<<2 * ka * kb, 256, 0, st>>>(part, nb, 1, reinterpret_cast<double *>(G));
     qs_note_launches(2);
     return cudaGetLastError();
 }
 
-cudaError_t qs_rotate(const double *W, int ka, const double2 *C, int kc, int64_t nr, double *V, cudaStream_t st)
+cudaError_t qs_rotate(const double *W, int ka, const double2 *C, int kc, int64_t nr, double *V, cudaStream_t st,
+                      int lowp)
 {
     int64_t nc = nr / 2;
     size_t sm = (size_t)ka * kc * sizeof(double2);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
+        cudaFuncSetAttribute(rotate_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
+        cudaFuncSetAttribute(rotate_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
         attr = true;
     }
-    rotate_kernel<<<grid_for(nc, 256), 256, sm, st>>>(W, ka, C, kc, nc, V);
+    if (lowp) rotate_kernel<true><<<grid_for(nc, 256), 256, sm, st>>>(W, ka, C, kc, nc, V);
+    else rotate_kernel<false><<<grid_for(nc, 256), 256, sm, st>>>(W, ka, C, kc, nc, V);
     qs_note_launches(1);
     return cudaGetLastError();
 }

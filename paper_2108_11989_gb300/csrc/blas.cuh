@@ -14,12 +14,14 @@ cudaError_t qs_dot(const R *a, const R *b, int k, int64_t nr, double *part, doub
 // out[r] = || a_r - theta[r] b_r ||^2 (FP64 vectors, theta on device)
 cudaError_t qs_resid2(const double *a, const double *b, const double *theta, int k, int64_t nr,
                       double *part, double *out, cudaStream_t st);
-// G[i][j] = <A_i, B_j>, i < ka, j < kb, complex row-major [ka][kb] (FP64 vectors)
+// G[i][j] = <A_i, B_j>, i < ka, j < kb, complex row-major [ka][kb] (FP64 vectors);
+// lowp: products and per-chunk sums in FP32, chunk sums accumulated in FP64
 cudaError_t qs_gram(const double *A, int ka, const double *B, int kb, int64_t nr, double *part,
-                    double2 *G, cudaStream_t st);
-// V_j = sum_i W_i C[i][j], j < kc (C complex row-major [ka][kc]); V must not alias W
+                    double2 *G, cudaStream_t st, int lowp = 0);
+// V_j = sum_i W_i C[i][j], j < kc (C complex row-major [ka][kc]); V must not alias W;
+// lowp: the k-term sums in FP32
 cudaError_t qs_rotate(const double *W, int ka, const double2 *C, int kc, int64_t nr, double *V,
-                      cudaStream_t st);
+                      cudaStream_t st, int lowp = 0);
 // y_r = (float)(x_r * scale[r])  (scale on device, may be NULL for 1)
 cudaError_t qs_d2f(const double *x, float *y, const double *scale, int k, int64_t nr, cudaStream_t st);
 // x_r += coef[r] * (double) e_r  (coef on device)

@@ -178,10 +178,10 @@ DslashArgs<float> make_args<float>(qs_lattice *lat, const double *m0, const void
 
 template <typename R>
 static int run_typed(qs_lattice *lat, int pi, const double *m0, const void *in, void *out, int nrhs,
-                     int gamma5)
+                     int gamma5, int soa)
 {
     DslashArgs<R> d = make_args<R>(lat, m0, in, out, nrhs, gamma5);
-    int &tv = lat->tuned[pi][nrhs];
+    int &tv = lat->tuned[soa ? 1 : 0][pi][nrhs];
     if (tv == 0) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         QS_CUDA(cudaStreamIsCapturing(lat->stream, &cs));
@@ -194,9 +194,9 @@ static int run_typed(qs_lattice *lat, int pi, const double *m0, const void *in, 
             float best = 1e30f;
             int bv = 0;
             for (int v = 0; v < qs_dslash_nvariants<R>(); ++v) {
-                QS_CUDA(qs_dslash_launch<R>(d, nrhs, v, lat->stream));   // warm-up
+                QS_CUDA(qs_dslash_launch<R>(d, nrhs, v, soa, lat->stream));   // warm-up
                 QS_CUDA(cudaEventRecord(e0, lat->stream));
-                for (int rep = 0; rep < 3; ++rep) QS_CUDA(qs_dslash_launch<R>(d, nrhs, v, lat->stream));
+                for (int rep = 0; rep < 3; ++rep) QS_CUDA(qs_dslash_launch<R>(d, nrhs, v, soa, lat->stream));
                 QS_CUDA(cudaEventRecord(e1, lat->stream));
                 QS_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -216,7 +216,7 @@ static int run_typed(qs_lattice *lat, int pi, const double *m0, const void *in, 
         eb = prof_event(pf);
         QS_CUDA(cudaEventRecord(ea, lat->stream));
     }
-    cudaError_t e = qs_dslash_launch<R>(d, nrhs, tv - 1, lat->stream);
+    cudaError_t e = qs_dslash_launch<R>(d, nrhs, tv - 1, soa, lat->stream);
     qs_note_launches(1);
     if (pf) {
         QS_CUDA(cudaEventRecord(eb, lat->stream));
@@ -231,10 +231,10 @@ static int run_typed(qs_lattice *lat, int pi, const double *m0, const void *in, 
 }
 
 int qs_dslash_run(qs_lattice *lat, int prec, const double *m0, const void *in, void *out, int nrhs,
-                  int gamma5)
+                  int gamma5, int soa)
 {
-    if (prec == QS_F64) return run_typed<double>(lat, 0, m0, in, out, nrhs, gamma5);
-    if (prec == QS_F32) return run_typed<float>(lat, 1, m0, in, out, nrhs, gamma5);
+    if (prec == QS_F64) return run_typed<double>(lat, 0, m0, in, out, nrhs, gamma5, soa);
+    if (prec == QS_F32) return run_typed<float>(lat, 1, m0, in, out, nrhs, gamma5, soa);
     return QS_EINVAL;
 }
 

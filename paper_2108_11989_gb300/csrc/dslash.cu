@@ -51,6 +51,45 @@ __device__ __forceinline__ void store24<double>(double *__restrict__ p, const do
     for (int i = 0; i < 12; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
 }
 
+// Site access in either spinor layout.  Canonical (SOA = false): [site][12][re, im].
+// Solver layout (SOA = true): [site / 16][12][site % 16][re, im], so that the 16 or
+// 32 threads of a warp handling consecutive sites read each colour-spin component
+// as one contiguous 128 B (FP32) or 256 B (FP64) segment.
+template <bool SOA, typename R>
+__device__ __forceinline__ void ld_site(const R *__restrict__ base, int64_t s, R v[24])
+{
+    if (!SOA) {
+        load24<R>(base + s * 24, v);
+    } else {
+        typedef typename LinkT<R>::T V2;
+        const V2 *b2 = reinterpret_cast<const V2 *>(base) + ((s >> 4) * 12) * 16 + (s & 15);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            V2 a = __ldg(b2 + c * 16);
+            v[2 * c] = a.x;
+            v[2 * c + 1] = a.y;
+        }
+    }
+}
+
+template <bool SOA, typename R>
+__device__ __forceinline__ void st_site(R *__restrict__ base, int64_t s, const R v[24])
+{
+    if (!SOA) {
+        store24<R>(base + s * 24, v);
+    } else {
+        typedef typename LinkT<R>::T V2;
+        V2 *b2 = reinterpret_cast<V2 *>(base) + ((s >> 4) * 12) * 16 + (s & 15);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            V2 a;
+            a.x = v[2 * c];
+            a.y = v[2 * c + 1];
+            b2[c * 16] = a;
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ C2<R> sp(const R v[24], int s, int c)
 {
@@ -156,7 +195,7 @@ __device__ __forceinline__ void mul_link_dag(const C2<R> U[9], bool cj, const C2
         }
 }
 
-template <int MU, typename R>
+template <int MU, bool SOA, typename R>
 __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restrict__ in, int64_t s,
                                         int64_t p, bool mir, C2<R> acc[12])
 {
@@ -167,7 +206,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restr
     {
         int64_t sf = qs_nbr(g, s, MU, +1, &sg);
         R v[24];
-        load24<R>(in + sf * 24, v);
+        ld_site<SOA, R>(in, sf, v);
         load_link<R>(a.links, g.Vphys, MU, p, U);
         C2<R> h[2][3], x[2][3];
         project<MU, true, R>(v, h);
@@ -186,7 +225,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restr
         bool mb;
         int64_t pb = qs_phys(g, sb, &mb);
         R v[24];
-        load24<R>(in + sb * 24, v);
+        ld_site<SOA, R>(in, sb, v);
         load_link<R>(a.links, g.Vphys, MU, pb, U);
         C2<R> h[2][3], x[2][3];
         project<MU, false, R>(v, h);
@@ -201,16 +240,17 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restr
     }
 }
 
-// One thread per (doubled site, right-hand side); the right-hand side index runs
-// fastest, so the threads of one site sit next to each other and share the link
-// and SW-term loads through L1.
-template <typename R, int MINB>
+// One thread per (doubled site, right-hand side).  A block handles 128 consecutive
+// sites of one right-hand side; the right-hand side runs fastest over consecutive
+// blocks, so the blocks of one site tile run together and share the link and
+// SW-term loads through L1/L2.
+template <typename R, int MINB, bool SOA>
 __global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
 {
     const Geom &g = a.g;
-    int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t s = tid / a.nrhs;
-    int r = (int)(tid - s * a.nrhs);
+    const int64_t b = blockIdx.x;
+    const int r = (int)(b % a.nrhs);
+    const int64_t s = (b / a.nrhs) * 128 + threadIdx.x;
     if (s >= g.Ns) return;
     const R *in = a.in + (int64_t)r * g.Ns * 24;
     bool mir;
@@ -219,10 +259,10 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
     C2<R> acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = cmk(R(0), R(0));
-    hop_dir<0, R>(a, in, s, p, mir, acc);
-    hop_dir<1, R>(a, in, s, p, mir, acc);
-    hop_dir<2, R>(a, in, s, p, mir, acc);
-    hop_dir<3, R>(a, in, s, p, mir, acc);
+    hop_dir<0, SOA, R>(a, in, s, p, mir, acc);
+    hop_dir<1, SOA, R>(a, in, s, p, mir, acc);
+    hop_dir<2, SOA, R>(a, in, s, p, mir, acc);
+    hop_dir<3, SOA, R>(a, in, s, p, mir, acc);
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = R(-0.5) * acc[i];
 
@@ -230,7 +270,7 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
     // Mirror sites use A' = S conj(A) S, S = s_2 (x) 1, i.e.
     // A'[i][j] = (same spin half ? 1 : -1) * conj(A[i +- 3][j +- 3]).
     R v[24];
-    load24<R>(in + s * 24, v);
+    ld_site<SOA, R>(in, s, v);
     const R dm = R(4) + (R)a.m0[r];
     const R *cl = a.clov + p;
     const int64_t V = g.Vphys;
@@ -272,48 +312,66 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
         o[2 * i] = f * acc[i].re;
         o[2 * i + 1] = f * acc[i].im;
     }
-    store24<R>(a.out + ((int64_t)r * g.Ns + s) * 24, o);
+    st_site<SOA, R>(a.out + (int64_t)r * g.Ns * 24, s, o);
 }
 
 }  // namespace
 
 template <typename R, int MINB>
-static cudaError_t launch_variant(const DslashArgs<R> &a, cudaStream_t st)
+static cudaError_t launch_variant(const DslashArgs<R> &a, int soa, cudaStream_t st)
 {
-    int64_t nt = a.g.Ns * a.nrhs;
-    int nb = (int)((nt + 127) / 128);
-    dslash_kernel<R, MINB><<<nb, 128, 0, st>>>(a);
+    int64_t nb = ((a.g.Ns + 127) / 128) * a.nrhs;
+    if (soa) dslash_kernel<R, MINB, true><<<(unsigned)nb, 128, 0, st>>>(a);
+    else dslash_kernel<R, MINB, false><<<(unsigned)nb, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 // Launch-bound variants (minimum resident 128-thread blocks per SM); the
-// autotuner in capi.cu picks one per (precision, nrhs) by timing.
+// autotuner in capi.cu picks one per (layout, precision, nrhs) by timing.
 template <>
 int qs_dslash_nvariants<float>() { return 5; }
 template <>
 int qs_dslash_nvariants<double>() { return 4; }
 
 template <>
-cudaError_t qs_dslash_launch<float>(DslashArgs<float> a, int nrhs, int variant, cudaStream_t st)
+cudaError_t qs_dslash_launch<float>(DslashArgs<float> a, int nrhs, int variant, int soa, cudaStream_t st)
 {
     a.nrhs = nrhs;
     switch (variant) {
-    case 0: return launch_variant<float, 3>(a, st);
-    case 1: return launch_variant<float, 4>(a, st);
-    case 2: return launch_variant<float, 5>(a, st);
-    case 3: return launch_variant<float, 6>(a, st);
-    default: return launch_variant<float, 8>(a, st);
+    case 0: return launch_variant<float, 3>(a, soa, st);
+    case 1: return launch_variant<float, 4>(a, soa, st);
+    case 2: return launch_variant<float, 5>(a, soa, st);
+    case 3: return launch_variant<float, 6>(a, soa, st);
+    default: return launch_variant<float, 8>(a, soa, st);
     }
 }
 
 template <>
-cudaError_t qs_dslash_launch<double>(DslashArgs<double> a, int nrhs, int variant, cudaStream_t st)
+cudaError_t qs_dslash_launch<double>(DslashArgs<double> a, int nrhs, int variant, int soa, cudaStream_t st)
 {
     a.nrhs = nrhs;
     switch (variant) {
-    case 0: return launch_variant<double, 1>(a, st);
-    case 1: return launch_variant<double, 2>(a, st);
-    case 2: return launch_variant<double, 3>(a, st);
-    default: return launch_variant<double, 4>(a, st);
+    case 0: return launch_variant<double, 1>(a, soa, st);
+    case 1: return launch_variant<double, 2>(a, soa, st);
+    case 2: return launch_variant<double, 3>(a, soa, st);
+    default: return launch_variant<double, 4>(a, soa, st);
     }
+}
+
+// canonical [site][12][re, im] <-> solver [site / 16][12][site % 16][re, im], per vector
+__global__ void soa_to_aos_kernel(const double2 *__restrict__ in, double2 *__restrict__ out, int64_t Ns)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;   // canonical complex index
+    if (i >= Ns * 12) return;
+    int64_t s = i / 12;
+    int c = (int)(i % 12);
+    out[i] = in[((s >> 4) * 12 + c) * 16 + (s & 15)];
+}
+
+cudaError_t qs_soa_to_aos(const double *in, double *out, int64_t Ns, cudaStream_t st)
+{
+    int64_t n = Ns * 12;
+    soa_to_aos_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double2 *)in, (double2 *)out, Ns);
+    qs_note_launches(1);
+    return cudaGetLastError();
 }

@@ -22,12 +22,16 @@ struct DslashArgs {
 
 // out = D in (or Q in) for nrhs vectors with launch variant `variant`
 // (0 .. qs_dslash_nvariants<R>() - 1); in and out must not overlap.
+// soa = 1: the solver's site-tiled spinor layout [site / 16][12][site % 16][re, im]
 template <typename R>
-cudaError_t qs_dslash_launch(DslashArgs<R> a, int nrhs, int variant, cudaStream_t st);
+cudaError_t qs_dslash_launch(DslashArgs<R> a, int nrhs, int variant, int soa, cudaStream_t st);
 template <typename R>
 int qs_dslash_nvariants();
 
 // Picks (and caches in the handle) the fastest variant for this precision and
 // nrhs by timing each once on the handle's stream, then launches it.
 int qs_dslash_run(qs_lattice *lat, int prec, const double *m0, const void *in, void *out,
-                  int nrhs, int gamma5);
+                  int nrhs, int gamma5, int soa = 0);
+
+// one vector from the solver layout to the canonical layout (FP64)
+cudaError_t qs_soa_to_aos(const double *in, double *out, int64_t Ns, cudaStream_t st);

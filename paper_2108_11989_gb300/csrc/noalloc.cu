@@ -40,9 +40,9 @@ static int run(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, 
     }
     // the variant the autotuner already chose, else a fixed one (timing the
     // variants would create events)
-    int tv = lat->tuned[pi][nrhs];
+    int tv = lat->tuned[0][pi][nrhs];
     int variant = tv > 0 ? tv - 1 : (qs_dslash_nvariants<R>() > 2 ? 2 : 0);
-    QS_CUDA(qs_dslash_launch<R>(d, nrhs, variant, lat->stream));
+    QS_CUDA(qs_dslash_launch<R>(d, nrhs, variant, 0, lat->stream));
     QS_CUDA(qs_norm2<R>((const R *)out, nrhs, lat->g.Ns * 24, scratch, norm2, lat->stream));
     return QS_OK;
 }

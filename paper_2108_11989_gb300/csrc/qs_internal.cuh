@@ -50,8 +50,8 @@ struct qs_lattice {
     // Hermitian blocks); the mirror site's blocks are derived on the fly
     double *clov64;
     float *clov32;
-    // autotuned Dslash launch variant + 1 per [precision][nrhs] (0: not tuned yet)
-    int tuned[2][65];
+    // autotuned Dslash launch variant + 1 per [layout][precision][nrhs] (0: not tuned)
+    int tuned[2][2][65];
     // solver workspace (allocated on first use, see solver.cu)
     struct Workspace *ws;
     // kernel profiling state (capi.cu), NULL when off

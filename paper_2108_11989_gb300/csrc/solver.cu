@@ -103,7 +103,7 @@ static int opQ(qs_lattice *lat, Workspace *w, int prec, double m0, const void *i
     double m[QS_MAX_RHS];
     for (int r = 0; r < k; ++r) m[r] = m0;
     if (prec == QS_F32) w->f32_count += k; else w->f64_count += k;
-    return qs_dslash_run(lat, prec, m, in, out, k, 1);
+    return qs_dslash_run(lat, prec, m, in, out, k, 1, 1);   // solver layout
 }
 
 static int opQ2(qs_lattice *lat, Workspace *w, int prec, double m0, const void *in, void *tmp, void *out, int k)
@@ -121,7 +121,9 @@ static int sync_read(qs_lattice *lat, Workspace *w, int slot, int n)
 }
 
 // column scaling + Cholesky-QR twice: X becomes orthonormal (tmp is clobbered)
-static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp, int k)
+// lowp: FP32 Gram and rotation (filter stage, where the block is far from
+// converged and FP32 rounding is far below its residuals)
+static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp, int k, int lowp)
 {
     cudaStream_t st = lat->stream;
     CK(qs_norm2<double>(X, k, w->nr, w->part, DS(w, S_TMP), st));
@@ -129,9 +131,9 @@ static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp,
     CK(qs_scale_cols(X, DS(w, S_COEF), k, w->nr, st));
     for (int pass = 0; pass < 2; ++pass) {
         double *src = pass == 0 ? X : tmp, *dst = pass == 0 ? tmp : X;
-        CK(qs_gram(src, k, src, k, w->nr, w->part, w->G, st));
+        CK(qs_gram(src, k, src, k, w->nr, w->part, w->G, st, lowp));
         CK(qs_chol_rinv(w->G, k, w->Rinv, w->di + 64 + pass, st));
-        CK(qs_rotate(src, k, w->Rinv, k, w->nr, dst, st));
+        CK(qs_rotate(src, k, w->Rinv, k, w->nr, dst, st, lowp));
     }
     return QS_OK;
 }
@@ -157,12 +159,13 @@ static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *
         CK(cudaMemsetAsync(w->blk64[1], 0, (size_t)k * w->nr * sizeof(double), st));
         CK(qs_axpy_f2d(w->blk64[1], w->blk32[1], DS(w, S_ONES), k, w->nr, st));
     }
-    CK(qs_gram(w->blk64[1], k, w->blk64[1], k, w->nr, w->part, w->Hm, st));
+    const int lowp = prec == QS_F32;
+    CK(qs_gram(w->blk64[1], k, w->blk64[1], k, w->nr, w->part, w->Hm, st, lowp));
     CK(qs_herm_eig(w->Hm, k, DS(w, S_RN), w->Ym, w->di + 66, st));
-    CK(qs_gram(w->blk64[0], k, w->blk64[1], k, w->nr, w->part, w->Hm, st));
+    CK(qs_gram(w->blk64[0], k, w->blk64[1], k, w->nr, w->part, w->Hm, st, lowp));
     CK(qs_herm_eig(w->Hm, k, DS(w, S_THETA), w->Ym, w->di + 67, st));
-    CK(qs_rotate(w->blk64[0], k, w->Ym, k, w->nr, w->blk64[2], st));
-    CK(qs_rotate(w->blk64[1], k, w->Ym, k, w->nr, w->blk64[3], st));
+    CK(qs_rotate(w->blk64[0], k, w->Ym, k, w->nr, w->blk64[2], st, lowp));
+    CK(qs_rotate(w->blk64[1], k, w->Ym, k, w->nr, w->blk64[3], st, lowp));
     std::swap(w->blk64[0], w->blk64[2]);
     std::swap(w->blk64[1], w->blk64[3]);
     CK(qs_resid2(w->blk64[1], w->blk64[0], DS(w, S_THETA), k, w->nr, w->part, DS(w, S_TMP), st));
@@ -317,7 +320,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         CK(qs_fill_gauss(w->blk64[0], (int64_t)k * w->nr, o->seed * 0x9E3779B97F4A7C15ULL + 17, st));
     }
     w->have_V = 0;
-    QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k));
+    QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, 1));
     QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F32));
     // b >= lambda_max(Q^2): ||Q|| = ||D|| <= max_x ||4 + m0 + A(x)|| + ||hopping||,
     // ||hopping|| <= 4 (each direction is a partial isometry pair of norm 1)
@@ -353,7 +356,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             std::swap(w->blk64[0], w->blk64[2]);
             CK(qs_fill_gauss(w->blk64[0] + (size_t)nconv * w->nr, (int64_t)(k - nconv) * w->nr,
                              o->seed * 0x2545F4914F6CDD1DULL + 977 * (restarts + 1), st));
-            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k));
+            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, 1));
             QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F32));
             last_prec = QS_F32;
             stall = fstall = 0;
@@ -368,7 +371,8 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
                     worst <= o->tol ? "done" : (refine ? "refine" : "filter"));
         if (worst <= o->tol) {
             if (last_prec == QS_F64) { *conv = 1; break; }
-            // confirm with the FP64 operator before accepting
+            // confirm with the FP64 operator (and an FP64-orthonormal block) before accepting
+            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, 0));
             QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F64));
             last_prec = QS_F64;
             continue;
@@ -401,10 +405,10 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             std::swap(w->blk64[0], w->blk64[2]);
             ++nref;
         }
-        QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k));
-        // FP32 operator while the block is far from converged (its residuals are then
-        // far above FP32 rounding); FP64 from the refinement stage on
+        // FP32 operator, Gram and rotation while the block is far from converged (its
+        // residuals are then far above FP32 rounding); FP64 from the refinement on
         last_prec = (refine || worst < 1e-3) ? QS_F64 : QS_F32;
+        QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, last_prec == QS_F32));
         QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, last_prec));
         double nw = 0;
         for (int i = 0; i < o->nwant; ++i)
@@ -442,11 +446,11 @@ extern "C" int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts
     int conv = 0;
     QS_TRY(qs_lowmodes_impl(lat, m0, &o, &rz, &conv, stats));
     for (int i = 0; i < o.k; ++i) { evals[i] = rz.theta[i]; resid[i] = rz.res[i]; }
-    if (evecs) {   // Ritz vectors in the order of the returned values
-        const size_t colb = (size_t)lat->ws->nr * sizeof(double);
+    if (evecs) {   // Ritz vectors in the order of the returned values, canonical layout
+        const size_t nr = lat->ws->nr;
         for (int i = 0; i < o.k; ++i)
-            CK(cudaMemcpyAsync((char *)evecs + i * colb, lat->ws->blk64[0] + (size_t)rz.col[i] * lat->ws->nr,
-                               colb, cudaMemcpyDeviceToDevice, lat->stream));
+            CK(qs_soa_to_aos(lat->ws->blk64[0] + (size_t)rz.col[i] * nr, (double *)evecs + (size_t)i * nr,
+                             lat->g.Ns, lat->stream));
         CK(cudaStreamSynchronize(lat->stream));
     }
     return conv ? QS_OK : QS_ENOCONV;
