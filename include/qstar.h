@@ -59,10 +59,15 @@ enum qs_status {
 
 enum qs_prec { QS_F64 = 0, QS_F32 = 1 };
 
+/* OR into the prec argument of qs_apply_Dw / qs_apply_Q to pass spinors in the
+ * solver's site-tiled layout [rhs][site / 16][spin-colour 12][site % 16][re, im]
+ * (site = canonical site index) instead of the canonical one. */
+#define QS_LAYOUT_TILED 16
+
 typedef struct qs_lattice qs_lattice;
 
 typedef struct {
-    int L, T;            /* physical extents; L even, L >= 2, T >= 2 */
+    int L, T;            /* physical extents; L even, L >= 2, T >= 2, 2 L^3 T < 2^30 */
     int cstar_mask;      /* bit k-1: C* in spatial direction k (bit 0 = x, required) */
     int t_antiperiodic;  /* 0: periodic in time (Sec. 2), 1: antiperiodic for fermions */
     int device;          /* CUDA device ordinal */
@@ -86,8 +91,9 @@ QS_API int qs_load_gauge(qs_lattice *lat, const double *su3, const double *u1_th
                   double csw_su3, double csw_u1);
 
 /* out = D(m0) in for nrhs vectors (Sec. 2 operator on the doubled lattice, Sec. 3).
- * in, out: device buffers of nrhs * N_s * 24 reals, canonical layout, in precision
- * prec (QS_F64: double, arithmetic in FP64; QS_F32: float, arithmetic in FP32).
+ * in, out: device buffers of nrhs * N_s * 24 reals, canonical layout (or the tiled one
+ * with QS_LAYOUT_TILED), in precision prec (QS_F64: double, arithmetic in FP64; QS_F32:
+ * float, arithmetic in FP32).
  * Asynchronous on the handle's stream. */
 QS_API int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec);
 

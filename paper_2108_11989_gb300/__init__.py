@@ -18,6 +18,7 @@ __all__ = ["QStarError", "Lattice", "create_lattice", "load_gauge", "apply_Dw", 
            "strerror", "QS_F64", "QS_F32", "lib"]
 
 QS_F64, QS_F32 = 0, 1
+QS_LAYOUT_TILED = 16
 
 
 class QStarError(RuntimeError):
@@ -163,15 +164,27 @@ def _nrhs(h, t):
     return n
 
 
-def apply_Dw(h, m0, inp, out):
-    """qs_apply_Dw on device tensors (float64 or float32, canonical layout)."""
+def apply_Dw(h, m0, inp, out, tiled=False):
+    """qs_apply_Dw on device tensors (float64 or float32; canonical layout, or the
+    site-tiled one with tiled=True)."""
     _check(_lib.qs_apply_Dw(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
-                            _prec_of(inp)), "apply_Dw")
+                            _prec_of(inp) | (QS_LAYOUT_TILED if tiled else 0)), "apply_Dw")
 
 
-def apply_Q(h, m0, inp, out):
+def apply_Q(h, m0, inp, out, tiled=False):
     _check(_lib.qs_apply_Q(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
-                           _prec_of(inp)), "apply_Q")
+                           _prec_of(inp) | (QS_LAYOUT_TILED if tiled else 0)), "apply_Q")
+
+
+def to_tiled(x, n_sites):
+    """Canonical [rhs][site][12][2] -> tiled [rhs][site/16][12][site%16][2] (torch, any device)."""
+    n = x.numel() // (n_sites * 24)
+    return x.reshape(n, n_sites // 16, 16, 12, 2).permute(0, 1, 3, 2, 4).contiguous().reshape(-1)
+
+
+def from_tiled(x, n_sites):
+    n = x.numel() // (n_sites * 24)
+    return x.reshape(n, n_sites // 16, 12, 16, 2).permute(0, 1, 3, 2, 4).contiguous().reshape(-1)
 
 
 def eig_default_opts(**kw):
@@ -259,11 +272,11 @@ class Lattice:
     def load_gauge(self, su3, theta, csw_su3, csw_u1):
         load_gauge(self.h, su3, theta, csw_su3, csw_u1)
 
-    def apply_Dw(self, m0, inp, out):
-        apply_Dw(self.h, m0, inp, out)
+    def apply_Dw(self, m0, inp, out, tiled=False):
+        apply_Dw(self.h, m0, inp, out, tiled)
 
-    def apply_Q(self, m0, inp, out):
-        apply_Q(self.h, m0, inp, out)
+    def apply_Q(self, m0, inp, out, tiled=False):
+        apply_Q(self.h, m0, inp, out, tiled)
 
     def lowmodes_at_mass(self, m0, opts=None, evecs=None, allow_noconv=False):
         return lowmodes_at_mass(self.h, m0, opts, evecs, allow_noconv)

@@ -124,8 +124,8 @@ extern "C" int qs_create_lattice(const qs_geom *geom, void *stream, qs_lattice *
     if (geom->L < 2 || (geom->L & 1) || geom->T < 2 || !(geom->cstar_mask & 1) ||
         geom->cstar_mask < 0 || geom->cstar_mask > 7)
         return QS_EINVAL;
-    // index arithmetic is 64-bit; keep N_s * 24 below 2^62
-    if ((double)geom->L * geom->L * geom->L * geom->T * 48.0 > 4.0e18) return QS_EINVAL;
+    // the operator indexes sites in 32-bit arithmetic: N_s = 2 L^3 T below 2^30
+    if (2.0 * geom->L * geom->L * geom->L * geom->T >= 1073741824.0) return QS_EINVAL;
     int ndev = 0;
     QS_CUDA(cudaGetDeviceCount(&ndev));
     if (geom->device < 0 || geom->device >= ndev) return QS_EINVAL;
@@ -243,13 +243,15 @@ int qs_apply_op(qs_lattice *lat, const double *m0, const void *in, void *out, in
 {
     if (!lat || !in || !out || nrhs < 1 || nrhs > QS_MAX_RHS) return QS_EINVAL;
     if (!lat->gauge_loaded) return QS_EINVAL;
+    const int tiled = (prec & QS_LAYOUT_TILED) ? 1 : 0;
+    prec &= ~QS_LAYOUT_TILED;
     if (prec != QS_F64 && prec != QS_F32) return QS_EINVAL;
     size_t bytes = (size_t)nrhs * lat->g.Ns * 24 * (prec == QS_F64 ? 8 : 4);
     const char *a = (const char *)in, *b = (const char *)out;
     if (a < b + bytes && b < a + bytes) return QS_EINVAL;      // overlap
     if (((uintptr_t)in | (uintptr_t)out) & 15) return QS_EINVAL; // vector loads need 16 B
     QS_CUDA(cudaSetDevice(lat->device));
-    return qs_dslash_run(lat, prec, m0, in, out, nrhs, gamma5);
+    return qs_dslash_run(lat, prec, m0, in, out, nrhs, gamma5, tiled);
 }
 
 extern "C" int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec)

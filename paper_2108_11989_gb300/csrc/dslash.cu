@@ -195,19 +195,80 @@ __device__ __forceinline__ void mul_link_dag(const C2<R> U[9], bool cj, const C2
         }
 }
 
+// Coordinates of a doubled site: x in [0, 2L), y, z in [0, L), t in [0, T);
+// row = (t L + z) L + y; p = row L + (x mod L) is the physical site.
+struct Site {
+    int s, x, y, z, t, row, p;
+};
+
+__device__ __forceinline__ Site site_of(const Geom &g, int s)
+{
+    Site c;
+    c.s = s;
+    c.row = s / g.L2;
+    c.x = s - c.row * g.L2;
+    int r = c.row;
+    c.y = r % g.L;
+    r /= g.L;
+    c.z = r % g.L;
+    c.t = r / g.L;
+    c.p = c.row * g.L + (c.x >= g.L ? c.x - g.L : c.x);
+    return c;
+}
+
+struct Nb {
+    int s, p;
+    bool mir;
+};
+
+// neighbour x + STEP mu (same rules as qs_nbr: x periodic over 2L; crossing y or z
+// with C* there also moves x by L; t periodic or antiperiodic)
+template <int MU, int STEP>
+__device__ __forceinline__ Nb nbr_of(const Geom &g, const Site &c, int *sg)
+{
+    int x = c.x, row = c.row;
+    *sg = 1;
+    const int L = g.L, L2 = g.L2;
+    if (MU == 0) {
+        const int LL = L * L;
+        if (STEP > 0) row = (c.t == g.T - 1) ? row - (g.T - 1) * LL : row + LL;
+        else row = (c.t == 0) ? row + (g.T - 1) * LL : row - LL;
+        if (g.t_anti && ((STEP > 0 && c.t == g.T - 1) || (STEP < 0 && c.t == 0))) *sg = -1;
+    } else if (MU == 1) {
+        if (STEP > 0) x = (x == L2 - 1) ? 0 : x + 1;
+        else x = (x == 0) ? L2 - 1 : x - 1;
+    } else {
+        const int coord = MU == 2 ? c.y : c.z;
+        const int stride = MU == 2 ? 1 : L;
+        const int cst = MU == 2 ? g.cstar_y : g.cstar_z;
+        bool wrap = STEP > 0 ? (coord == L - 1) : (coord == 0);
+        if (wrap) {
+            row += STEP > 0 ? -(L - 1) * stride : (L - 1) * stride;
+            if (cst) x = x >= L ? x - L : x + L;
+        } else {
+            row += STEP * stride;
+        }
+    }
+    Nb n;
+    n.s = row * L2 + x;
+    n.mir = x >= L;
+    n.p = row * L + (n.mir ? x - L : x);
+    return n;
+}
+
 template <int MU, bool SOA, typename R>
-__device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restrict__ in, int64_t s,
-                                        int64_t p, bool mir, C2<R> acc[12])
+__device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restrict__ in, const Site &c,
+                                        bool mir, C2<R> acc[12])
 {
     const Geom &g = a.g;
     C2<R> U[9];
-    int sg;
     // forward: V(x, mu) (1 - g_mu) psi(x + mu)
     {
-        int64_t sf = qs_nbr(g, s, MU, +1, &sg);
+        int sg;
+        Nb n = nbr_of<MU, +1>(g, c, &sg);
         R v[24];
-        ld_site<SOA, R>(in, sf, v);
-        load_link<R>(a.links, g.Vphys, MU, p, U);
+        ld_site<SOA, R>(in, n.s, v);
+        load_link<R>(a.links, g.Vphys, MU, c.p, U);
         C2<R> h[2][3], x[2][3];
         project<MU, true, R>(v, h);
         mul_link<R>(U, mir, h, x);
@@ -215,26 +276,25 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restr
 #pragma unroll
             for (int q = 0; q < 2; ++q)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) x[q][c] = cmk(-x[q][c].re, -x[q][c].im);
+                for (int cc = 0; cc < 3; ++cc) x[q][cc] = cmk(-x[q][cc].re, -x[q][cc].im);
         }
         reconstruct<MU, true, R>(acc, x);
     }
     // backward: V(x - mu, mu)^+ (1 + g_mu) psi(x - mu)
     {
-        int64_t sb = qs_nbr(g, s, MU, -1, &sg);
-        bool mb;
-        int64_t pb = qs_phys(g, sb, &mb);
+        int sg;
+        Nb n = nbr_of<MU, -1>(g, c, &sg);
         R v[24];
-        ld_site<SOA, R>(in, sb, v);
-        load_link<R>(a.links, g.Vphys, MU, pb, U);
+        ld_site<SOA, R>(in, n.s, v);
+        load_link<R>(a.links, g.Vphys, MU, n.p, U);
         C2<R> h[2][3], x[2][3];
         project<MU, false, R>(v, h);
-        mul_link_dag<R>(U, mb, h, x);
+        mul_link_dag<R>(U, n.mir, h, x);
         if (MU == 0 && sg < 0) {
 #pragma unroll
             for (int q = 0; q < 2; ++q)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) x[q][c] = cmk(-x[q][c].re, -x[q][c].im);
+                for (int cc = 0; cc < 3; ++cc) x[q][cc] = cmk(-x[q][cc].re, -x[q][cc].im);
         }
         reconstruct<MU, false, R>(acc, x);
     }
@@ -243,26 +303,29 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restr
 // One thread per (doubled site, right-hand side).  A block handles 128 consecutive
 // sites of one right-hand side; the right-hand side runs fastest over consecutive
 // blocks, so the blocks of one site tile run together and share the link and
-// SW-term loads through L1/L2.
+// SW-term loads through L1/L2.  Site coordinates are computed once per thread in
+// 32-bit arithmetic; every neighbour and physical index follows by adds and
+// compares (no division in the stencil).
 template <typename R, int MINB, bool SOA>
 __global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
 {
     const Geom &g = a.g;
-    const int64_t b = blockIdx.x;
-    const int r = (int)(b % a.nrhs);
-    const int64_t s = (b / a.nrhs) * 128 + threadIdx.x;
-    if (s >= g.Ns) return;
+    const unsigned b = blockIdx.x;
+    const int r = (int)(b % (unsigned)a.nrhs);
+    const int s = (int)(b / (unsigned)a.nrhs) * 128 + (int)threadIdx.x;
+    if (s >= (int)g.Ns) return;
     const R *in = a.in + (int64_t)r * g.Ns * 24;
-    bool mir;
-    int64_t p = qs_phys(g, s, &mir);
+    Site c = site_of(g, s);
+    const int p = c.p;
+    const bool mir = c.x >= g.L;
 
     C2<R> acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = cmk(R(0), R(0));
-    hop_dir<0, SOA, R>(a, in, s, p, mir, acc);
-    hop_dir<1, SOA, R>(a, in, s, p, mir, acc);
-    hop_dir<2, SOA, R>(a, in, s, p, mir, acc);
-    hop_dir<3, SOA, R>(a, in, s, p, mir, acc);
+    hop_dir<0, SOA, R>(a, in, c, mir, acc);
+    hop_dir<1, SOA, R>(a, in, c, mir, acc);
+    hop_dir<2, SOA, R>(a, in, c, mir, acc);
+    hop_dir<3, SOA, R>(a, in, c, mir, acc);
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = R(-0.5) * acc[i];
 

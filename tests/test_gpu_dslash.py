@@ -138,3 +138,23 @@ def test_errors(qs):
     with pytest.raises(qs.QStarError):          # bad geometry: odd L
         qs.Lattice(3, 4)
     lat.close()
+
+
+@pytest.mark.parametrize("prec,nrhs", [("f64", 3), ("f32", 9)])
+def test_tiled_layout_matches_canonical(qs, prec, nrhs):
+    """The solver's site-tiled layout gives the same operator (9 RHS: a partial group of 8)."""
+    import torch
+    cfg = make_config(T=4, L=4, eps=0.5, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=13)
+    lat = qs.Lattice(cfg.L, cfg.T)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    psi = random_spinor(5, cfg.T, cfg.L, nrhs)
+    x = _to_dev(psi, dt).reshape(-1)
+    y = torch.empty_like(x)
+    lat.apply_Q(0.07, x, y)
+    xt = qs.to_tiled(x, cfg.n_sites)
+    yt = torch.empty_like(xt)
+    lat.apply_Q(0.07, xt, yt, tiled=True)
+    got = qs.from_tiled(yt, cfg.n_sites)
+    assert torch.equal(got, y)
+    lat.close()
