@@ -94,13 +94,21 @@ def dist_init():
 
 
 def max_over_ranks(x, ws):
+    """Max of a per-rank scalar (the timed region is the slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(bytes_per_rank, ms_per_rank, ws):
+    """Whole-job throughput: bytes of all ranks over the slowest rank's time (GB/s)."""
+    ms = max_over_ranks(ms_per_rank, ws)
+    return ws * bytes_per_rank / (ms * 1e-3) / 1e9, ms
 
 
 def barrier(ws):
