@@ -100,6 +100,26 @@ QS_API int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, in
 /* out = Q(m0) in = gamma_5 D(m0) in (Sec. 3).  Same arguments as qs_apply_Dw. */
 QS_API int qs_apply_Q(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec);
 
+/* Several configurations in ONE launch (the batched form of the hot path: many
+ * masses, several gauge configurations of uneven volume, blocks of vectors).
+ * items[i].out = Q(m0_r) items[i].in for every right-hand side r < items[i].nrhs,
+ * m0_r = items[i].m0[r] (host array).  Up to 8 items, up to 16 right-hand sides
+ * each, all lattices on one device with their gauge fields loaded; buffers as for
+ * qs_apply_Q (prec may carry QS_LAYOUT_TILED).  Runs on `stream` (a cudaStream_t or
+ * NULL).  Returns QS_EINVAL for more items / right-hand sides, mixed devices,
+ * overlapping in/out of an item. */
+#define QS_BATCH_MAX_ITEMS 8
+#define QS_BATCH_MAX_RHS 16
+typedef struct {
+    qs_lattice *lat;
+    const void *in;
+    void *out;
+    int nrhs;
+    const double *m0;   /* host, nrhs masses */
+} qs_batch_item;
+
+QS_API int qs_apply_Q_batch(const qs_batch_item *items, int n, int prec, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Low modes of Q(m0) (Sec. 3: lambda_bar = min_n |lambda_n| "by the power method
  * plus Chebyshev acceleration"; the eigenvalues closest to zero are what the

@@ -14,7 +14,7 @@ from .build import LIB
 
 __all__ = ["QStarError", "Lattice", "create_lattice", "load_gauge", "apply_Dw", "apply_Q",
            "lowmodes_at_mass", "pfaffian_sign", "eig_default_opts", "sign_default_opts",
-           "set_profiling", "get_profile",
+           "set_profiling", "get_profile", "apply_Q_batch",
            "strerror", "QS_F64", "QS_F32", "lib"]
 
 QS_F64, QS_F32 = 0, 1
@@ -32,6 +32,11 @@ class QStarError(RuntimeError):
 class _Geom(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("cstar_mask", ctypes.c_int),
                 ("t_antiperiodic", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("lat", ctypes.c_void_p), ("inp", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("nrhs", ctypes.c_int), ("m0", ctypes.POINTER(ctypes.c_double))]
 
 
 class EigOpts(ctypes.Structure):
@@ -102,6 +107,7 @@ def _load():
         "qs_set_profiling": (I, [P, I]),
         "qs_get_profile": (I, [P, ctypes.POINTER(Profile)]),
         "qs_kernel_launches": (ctypes.c_int64, []),
+        "qs_apply_Q_batch": (I, [ctypes.POINTER(BatchItem), I, I, P]),
         "qs_apply_Q_norm2_noalloc": (I, [P, D, P, P, I, I, P]),
         "qs_strerror": (ctypes.c_char_p, [I]),
         "qs_last_cuda_error": (ctypes.c_char_p, []),
@@ -239,6 +245,29 @@ def apply_Q_norm2_noalloc(h, m0, inp, out, norm2):
     with no device allocation by the library."""
     _check(_lib.qs_apply_Q_norm2_noalloc(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
                                          _prec_of(inp), norm2.data_ptr()), "apply_Q_norm2_noalloc")
+
+
+def apply_Q_batch(entries, tiled=False, stream=None):
+    """qs_apply_Q_batch: one launch over [(lattice, in, out, masses), ...]; masses has one
+    bare mass per right-hand side of that lattice's in/out tensors."""
+    n = len(entries)
+    arr = (BatchItem * n)()
+    keep = []
+    prec = None
+    for i, (lat, inp, out, masses) in enumerate(entries):
+        h = lat.h if hasattr(lat, "h") else lat
+        m = (ctypes.c_double * len(masses))(*[float(x) for x in masses])
+        keep.append(m)
+        nr = _nrhs(h, inp)
+        if nr != len(masses):
+            raise ValueError("one mass per right-hand side")
+        arr[i] = BatchItem(h, inp.data_ptr(), out.data_ptr(), nr, m)
+        p = _prec_of(inp)
+        if prec is not None and p != prec:
+            raise TypeError("all items of a batch share one precision")
+        prec = p
+    _check(_lib.qs_apply_Q_batch(arr, n, prec | (QS_LAYOUT_TILED if tiled else 0), _stream_ptr(stream)),
+           "apply_Q_batch")
 
 
 def kernel_launches():

@@ -286,3 +286,65 @@ extern "C" const char *qs_strerror(int status)
 }
 
 extern "C" const char *qs_last_cuda_error(void) { return g_last_cuda_error; }
+
+template <typename R>
+static int batch_typed(const qs_batch_item *items, int n, int tiled, cudaStream_t st)
+{
+    BatchArgs<R> a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.gamma5 = 1;
+    unsigned off = 0;
+    for (int i = 0; i < n; ++i) {
+        qs_lattice *lat = items[i].lat;
+        BatchItem<R> &it = a.item[i];
+        it.g = lat->g;
+        if (sizeof(R) == 8) {
+            it.links = (const typename LinkT<R>::T *)lat->links64;
+            it.clov = (const R *)lat->clov64;
+        } else {
+            it.links = (const typename LinkT<R>::T *)lat->links32;
+            it.clov = (const R *)lat->clov32;
+        }
+        it.in = (const R *)items[i].in;
+        it.out = (R *)items[i].out;
+        it.nrhs = items[i].nrhs;
+        for (int r = 0; r < it.nrhs; ++r) it.m0[r] = items[i].m0[r];
+        a.off[i] = off;
+        double nb = (double)((lat->g.Ns + 127) / 128) * it.nrhs;
+        if (off + nb > 2147483647.0) return QS_EINVAL;
+        off += (unsigned)nb;
+    }
+    a.off[n] = off;
+    cudaError_t e = qs_dslash_batch_launch<R>(a, tiled, st);
+    if (e != cudaSuccess) {
+        qs_record_cuda_error(e, "batched dslash launch");
+        return QS_ECUDA;
+    }
+    return QS_OK;
+}
+
+extern "C" int qs_apply_Q_batch(const qs_batch_item *items, int n, int prec, void *stream)
+{
+    if (!items || n < 1 || n > QS_BATCH_MAX) return QS_EINVAL;
+    const int tiled = (prec & QS_LAYOUT_TILED) ? 1 : 0;
+    prec &= ~QS_LAYOUT_TILED;
+    if (prec != QS_F64 && prec != QS_F32) return QS_EINVAL;
+    const size_t rs = prec == QS_F64 ? 8 : 4;
+    int dev = -1;
+    for (int i = 0; i < n; ++i) {
+        const qs_batch_item &it = items[i];
+        if (!it.lat || !it.in || !it.out || !it.m0 || it.nrhs < 1 || it.nrhs > QS_BATCH_RHS) return QS_EINVAL;
+        if (!it.lat->gauge_loaded) return QS_EINVAL;
+        if (dev >= 0 && it.lat->device != dev) return QS_EINVAL;
+        dev = it.lat->device;
+        size_t bytes = (size_t)it.nrhs * it.lat->g.Ns * 24 * rs;
+        const char *a = (const char *)it.in, *b = (const char *)it.out;
+        if (a < b + bytes && b < a + bytes) return QS_EINVAL;
+        if (((uintptr_t)it.in | (uintptr_t)it.out) & 15) return QS_EINVAL;
+    }
+    QS_CUDA(cudaSetDevice(dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == QS_F64) return batch_typed<double>(items, n, tiled, st);
+    return batch_typed<float>(items, n, tiled, st);
+}

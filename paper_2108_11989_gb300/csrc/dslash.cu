@@ -257,10 +257,9 @@ __device__ __forceinline__ Nb nbr_of(const Geom &g, const Site &c, int *sg)
 }
 
 template <int MU, bool SOA, typename R>
-__device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restrict__ in, const Site &c,
-                                        bool mir, C2<R> acc[12])
+__device__ __forceinline__ void hop_dir(const Geom &g, const typename LinkT<R>::T *__restrict__ links,
+                                        const R *__restrict__ in, const Site &c, bool mir, C2<R> acc[12])
 {
-    const Geom &g = a.g;
     C2<R> U[9];
     // forward: V(x, mu) (1 - g_mu) psi(x + mu)
     {
@@ -268,7 +267,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restr
         Nb n = nbr_of<MU, +1>(g, c, &sg);
         R v[24];
         ld_site<SOA, R>(in, n.s, v);
-        load_link<R>(a.links, g.Vphys, MU, c.p, U);
+        load_link<R>(links, g.Vphys, MU, c.p, U);
         C2<R> h[2][3], x[2][3];
         project<MU, true, R>(v, h);
         mul_link<R>(U, mir, h, x);
@@ -286,7 +285,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restr
         Nb n = nbr_of<MU, -1>(g, c, &sg);
         R v[24];
         ld_site<SOA, R>(in, n.s, v);
-        load_link<R>(a.links, g.Vphys, MU, n.p, U);
+        load_link<R>(links, g.Vphys, MU, n.p, U);
         C2<R> h[2][3], x[2][3];
         project<MU, false, R>(v, h);
         mul_link_dag<R>(U, n.mir, h, x);
@@ -306,15 +305,13 @@ __device__ __forceinline__ void hop_dir(const DslashArgs<R> &a, const R *__restr
 // SW-term loads through L1/L2.  Site coordinates are computed once per thread in
 // 32-bit arithmetic; every neighbour and physical index follows by adds and
 // compares (no division in the stencil).
-template <typename R, int MINB, bool SOA>
-__global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
+// D (or Q) at doubled site s for right-hand side r: the whole stencil of one site.
+template <typename R, bool SOA>
+__device__ __forceinline__ void dslash_site(const Geom &g, const typename LinkT<R>::T *__restrict__ links,
+                                            const R *__restrict__ clov, const R *__restrict__ in_all,
+                                            R *__restrict__ out_all, int gamma5, double m0, int r, int s)
 {
-    const Geom &g = a.g;
-    const unsigned b = blockIdx.x;
-    const int r = (int)(b % (unsigned)a.nrhs);
-    const int s = (int)(b / (unsigned)a.nrhs) * 128 + (int)threadIdx.x;
-    if (s >= (int)g.Ns) return;
-    const R *in = a.in + (int64_t)r * g.Ns * 24;
+    const R *in = in_all + (int64_t)r * g.Ns * 24;
     Site c = site_of(g, s);
     const int p = c.p;
     const bool mir = c.x >= g.L;
@@ -322,10 +319,10 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
     C2<R> acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = cmk(R(0), R(0));
-    hop_dir<0, SOA, R>(a, in, c, mir, acc);
-    hop_dir<1, SOA, R>(a, in, c, mir, acc);
-    hop_dir<2, SOA, R>(a, in, c, mir, acc);
-    hop_dir<3, SOA, R>(a, in, c, mir, acc);
+    hop_dir<0, SOA, R>(g, links, in, c, mir, acc);
+    hop_dir<1, SOA, R>(g, links, in, c, mir, acc);
+    hop_dir<2, SOA, R>(g, links, in, c, mir, acc);
+    hop_dir<3, SOA, R>(g, links, in, c, mir, acc);
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = R(-0.5) * acc[i];
 
@@ -334,8 +331,8 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
     // A'[i][j] = (same spin half ? 1 : -1) * conj(A[i +- 3][j +- 3]).
     R v[24];
     ld_site<SOA, R>(in, s, v);
-    const R dm = R(4) + (R)a.m0[r];
-    const R *cl = a.clov + p;
+    const R dm = R(4) + (R)m0;
+    const R *cl = clov + p;
     const int64_t V = g.Vphys;
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
@@ -368,14 +365,47 @@ __global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
         }
     }
     R o[24];
-    const R gs = a.gamma5 ? R(-1) : R(1);
+    const R gs = gamma5 ? R(-1) : R(1);
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
         R f = i >= 6 ? gs : R(1);
         o[2 * i] = f * acc[i].re;
         o[2 * i + 1] = f * acc[i].im;
     }
-    st_site<SOA, R>(a.out + (int64_t)r * g.Ns * 24, s, o);
+    st_site<SOA, R>(out_all + (int64_t)r * g.Ns * 24, s, o);
+}
+
+// One thread per (doubled site, right-hand side).  A block handles 128 consecutive
+// sites of one right-hand side; the right-hand side runs fastest over consecutive
+// blocks, so the blocks of one site tile run together and share the link and
+// SW-term loads through L1/L2.  Site coordinates are computed once per thread in
+// 32-bit arithmetic; every neighbour and physical index follows by adds and
+// compares (no division in the stencil).
+template <typename R, int MINB, bool SOA>
+__global__ void __launch_bounds__(128, MINB) dslash_kernel(DslashArgs<R> a)
+{
+    const unsigned b = blockIdx.x;
+    const int r = (int)(b % (unsigned)a.nrhs);
+    const int s = (int)(b / (unsigned)a.nrhs) * 128 + (int)threadIdx.x;
+    if (s >= (int)a.g.Ns) return;
+    dslash_site<R, SOA>(a.g, a.links, a.clov, a.in, a.out, a.gamma5, a.m0[r], r, s);
+}
+
+// Several lattices (configurations of any volume) in one launch: item i owns the
+// blocks [off[i], off[i + 1]), laid out as in dslash_kernel.
+template <typename R, bool SOA>
+__global__ void __launch_bounds__(128) dslash_batch_kernel(BatchArgs<R> a)
+{
+    const unsigned b = blockIdx.x;
+    int i = 0;
+#pragma unroll 1
+    while (i + 1 < a.n && b >= a.off[i + 1]) ++i;
+    const BatchItem<R> &it = a.item[i];
+    const unsigned lb = b - a.off[i];
+    const int r = (int)(lb % (unsigned)it.nrhs);
+    const int s = (int)(lb / (unsigned)it.nrhs) * 128 + (int)threadIdx.x;
+    if (s >= (int)it.g.Ns) return;
+    dslash_site<R, SOA>(it.g, it.links, it.clov, it.in, it.out, a.gamma5, it.m0[r], r, s);
 }
 
 }  // namespace
@@ -438,3 +468,15 @@ cudaError_t qs_soa_to_aos(const double *in, double *out, int64_t Ns, cudaStream_
     qs_note_launches(1);
     return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t qs_dslash_batch_launch(const BatchArgs<R> &a, int soa, cudaStream_t st)
+{
+    unsigned nb = a.off[a.n];
+    if (soa) dslash_batch_kernel<R, true><<<nb, 128, 0, st>>>(a);
+    else dslash_batch_kernel<R, false><<<nb, 128, 0, st>>>(a);
+    qs_note_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t qs_dslash_batch_launch<float>(const BatchArgs<float> &, int, cudaStream_t);
+template cudaError_t qs_dslash_batch_launch<double>(const BatchArgs<double> &, int, cudaStream_t);

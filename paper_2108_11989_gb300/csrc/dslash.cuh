@@ -20,6 +20,28 @@ struct DslashArgs {
     double m0[QS_MAX_RHS];                // bare mass per right-hand side
 };
 
+// batched form: up to QS_BATCH_MAX lattices, up to QS_BATCH_RHS right-hand sides each
+#define QS_BATCH_MAX 8
+#define QS_BATCH_RHS 16
+template <typename R>
+struct BatchItem {
+    Geom g;
+    const typename LinkT<R>::T *links;
+    const R *clov;
+    const R *in;
+    R *out;
+    int nrhs;
+    double m0[QS_BATCH_RHS];
+};
+template <typename R>
+struct BatchArgs {
+    int n, gamma5;
+    unsigned off[QS_BATCH_MAX + 1];   // first block of each item, off[n] = total blocks
+    BatchItem<R> item[QS_BATCH_MAX];
+};
+template <typename R>
+cudaError_t qs_dslash_batch_launch(const BatchArgs<R> &a, int soa, cudaStream_t st);
+
 // out = D in (or Q in) for nrhs vectors with launch variant `variant`
 // (0 .. qs_dslash_nvariants<R>() - 1); in and out must not overlap.
 // soa = 1: the solver's site-tiled spinor layout [site / 16][12][site % 16][re, im]

@@ -158,3 +158,35 @@ def test_tiled_layout_matches_canonical(qs, prec, nrhs):
     got = qs.from_tiled(yt, cfg.n_sites)
     assert torch.equal(got, y)
     lat.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_batched_configs_of_uneven_volume(qs, prec, tol):
+    """qs_apply_Q_batch: three configurations of different volumes, a mass per
+    right-hand side, in one launch = qs_apply_Q on each vector separately."""
+    import torch
+    dt = torch.float64 if prec == "f64" else torch.float32
+    cfgs = [make_config(T=4, L=4, eps=0.4, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=31),
+            make_config(T=6, L=4, eps=0.3, theta_sigma=0.2, csw_su3=1.9, csw_u1=1.0, seed=32),
+            make_config(T=4, L=6, eps=0.2, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=33)]
+    nrhs = [2, 3, 1]
+    masses = [[-0.3, 0.1], [0.05, -0.2, 0.4], [0.0]]
+    lats, items, refs = [], [], []
+    for cfg, nr, ms in zip(cfgs, nrhs, masses):
+        lat = qs.Lattice(cfg.L, cfg.T)
+        lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+        x = _to_dev(random_spinor(7 + nr, cfg.T, cfg.L, nr), dt).reshape(-1)
+        y = torch.full_like(x, float("nan"))
+        ref = torch.empty_like(x)
+        per = cfg.n_sites * 24
+        for r, m in enumerate(ms):
+            lat.apply_Q(m, x[r * per:(r + 1) * per], ref[r * per:(r + 1) * per])
+        lats.append(lat)
+        items.append((lat, x, y, ms))
+        refs.append(ref)
+    qs.apply_Q_batch(items)
+    torch.cuda.synchronize()
+    for (_, _, y, _), ref in zip(items, refs):
+        assert (y - ref).abs().max().item() <= tol * ref.abs().max().item()
+    for lat in lats:
+        lat.close()
