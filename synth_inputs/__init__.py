@@ -109,3 +109,18 @@ WORKLOADS = {
 def kappa_to_m0(kappa):
     """Bare mass from the hopping parameter, kappa = 1 / (2 (m0 + 4))."""
     return 1.0 / (2.0 * kappa) - 4.0
+
+
+def mlp_init(seed, n_in, n_hidden, n_out):
+    """Initial weights of the step-proposal network (random numbers only):
+    [W1 (n_hidden x n_in), b1, W2 (n_hidden x n_hidden), b2, W3 (n_out x n_hidden), b3],
+    W ~ N(0, 1/fan_in), b = 0, float32."""
+    rng = np.random.default_rng(seed)
+    shapes = [(n_hidden, n_in), (n_hidden,), (n_hidden, n_hidden), (n_hidden,), (n_out, n_hidden), (n_out,)]
+    out = []
+    for sh in shapes:
+        if len(sh) == 2:
+            out.append((rng.standard_normal(sh) / np.sqrt(sh[1])).astype(np.float32))
+        else:
+            out.append(np.zeros(sh, dtype=np.float32))
+    return out
