@@ -121,6 +121,32 @@ typedef struct {
 QS_API int qs_apply_Q_batch(const qs_batch_item *items, int n, int prec, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Step-proposal network (learned form of the flow; the paper steps with the fixed
+ * rule m <- m + c lambda_bar of Sec. 3).  A 3-layer FP32 perceptron
+ * in -> hidden -> hidden -> out with ReLU, trained on the GPU by the library's own
+ * forward, backward and Adam kernels.  Parameters (host layout, row-major FP32):
+ * [W1 (hidden x in), b1, W2 (hidden x hidden), b2, W3 (out x hidden), b3].
+ * Loss over B rows with targets T (column 0 regression, columns 1.. labels in [0, 1]):
+ *   L = (1/B) sum_b [ (Y_b0 - T_b0)^2 / 2 + sum_{j>=1} (softplus(Y_bj) - T_bj Y_bj) ].
+ * Adam with beta1 = 0.9, beta2 = 0.999, eps = 1e-8.  X, T, Y are DEVICE arrays.
+ * ------------------------------------------------------------------------- */
+typedef struct qs_mlp qs_mlp;
+/* on the current device; stream: cudaStream_t or NULL; parameters start at zero */
+QS_API int qs_mlp_create(int n_in, int n_hidden, int n_out, int max_batch, void *stream, qs_mlp **out);
+QS_API int qs_mlp_destroy(qs_mlp *net);
+QS_API int64_t qs_mlp_n_params(const qs_mlp *net);
+/* copy parameters in / out (host arrays of qs_mlp_n_params floats); set resets Adam */
+QS_API int qs_mlp_set_params(qs_mlp *net, const float *host);
+QS_API int qs_mlp_get_params(qs_mlp *net, float *host);
+/* gradients of the last qs_mlp_train_step (host array of qs_mlp_n_params floats) */
+QS_API int qs_mlp_get_grads(qs_mlp *net, float *host);
+/* Y [B][out] = network(X [B][in]), B <= max_batch */
+QS_API int qs_mlp_forward(qs_mlp *net, const float *X, int B, float *Y);
+/* one Adam step on the batch (X [B][in], T [B][out]); *loss (host, may be NULL) = L
+ * before the step */
+QS_API int qs_mlp_train_step(qs_mlp *net, const float *X, const float *T, int B, float lr, float *loss);
+
+/* ---------------------------------------------------------------------------
  * Low modes of Q(m0) (Sec. 3: lambda_bar = min_n |lambda_n| "by the power method
  * plus Chebyshev acceleration"; the eigenvalues closest to zero are what the
  * sign algorithm follows across masses).

@@ -14,7 +14,7 @@ from .build import LIB
 
 __all__ = ["QStarError", "Lattice", "create_lattice", "load_gauge", "apply_Dw", "apply_Q",
            "lowmodes_at_mass", "pfaffian_sign", "eig_default_opts", "sign_default_opts",
-           "set_profiling", "get_profile", "apply_Q_batch",
+           "set_profiling", "get_profile", "apply_Q_batch", "MLP",
            "strerror", "QS_F64", "QS_F32", "lib"]
 
 QS_F64, QS_F32 = 0, 1
@@ -107,6 +107,14 @@ def _load():
         "qs_set_profiling": (I, [P, I]),
         "qs_get_profile": (I, [P, ctypes.POINTER(Profile)]),
         "qs_kernel_launches": (ctypes.c_int64, []),
+        "qs_mlp_create": (I, [I, I, I, I, P, ctypes.POINTER(P)]),
+        "qs_mlp_destroy": (I, [P]),
+        "qs_mlp_n_params": (ctypes.c_int64, [P]),
+        "qs_mlp_set_params": (I, [P, P]),
+        "qs_mlp_get_params": (I, [P, P]),
+        "qs_mlp_get_grads": (I, [P, P]),
+        "qs_mlp_forward": (I, [P, P, I, P]),
+        "qs_mlp_train_step": (I, [P, P, P, I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
         "qs_apply_Q_batch": (I, [ctypes.POINTER(BatchItem), I, I, P]),
         "qs_apply_Q_norm2_noalloc": (I, [P, D, P, P, I, I, P]),
         "qs_strerror": (ctypes.c_char_p, [I]),
@@ -268,6 +276,66 @@ def apply_Q_batch(entries, tiled=False, stream=None):
         prec = p
     _check(_lib.qs_apply_Q_batch(arr, n, prec | (QS_LAYOUT_TILED if tiled else 0), _stream_ptr(stream)),
            "apply_Q_batch")
+
+
+class MLP:
+    """Owning wrapper around qs_mlp (the step-proposal network)."""
+
+    def __init__(self, n_in, n_hidden, n_out, max_batch, stream=None):
+        self.shape = (n_in, n_hidden, n_out)
+        self.h = ctypes.c_void_p()
+        _check(_lib.qs_mlp_create(n_in, n_hidden, n_out, max_batch, _stream_ptr(stream), ctypes.byref(self.h)),
+               "mlp_create")
+        self.n_params = _lib.qs_mlp_n_params(self.h)
+
+    def set_params(self, tensors):
+        flat = np.concatenate([np.asarray(t, dtype=np.float32).ravel() for t in tensors])
+        assert flat.size == self.n_params
+        _check(_lib.qs_mlp_set_params(self.h, flat.ctypes.data), "mlp_set_params")
+
+    def _split(self, flat):
+        ni, nh, no = self.shape
+        shapes = [(nh, ni), (nh,), (nh, nh), (nh,), (no, nh), (no,)]
+        out, o = [], 0
+        for sh in shapes:
+            n = int(np.prod(sh))
+            out.append(flat[o:o + n].reshape(sh))
+            o += n
+        return out
+
+    def get_params(self):
+        flat = np.empty(self.n_params, dtype=np.float32)
+        _check(_lib.qs_mlp_get_params(self.h, flat.ctypes.data), "mlp_get_params")
+        return self._split(flat)
+
+    def get_grads(self):
+        flat = np.empty(self.n_params, dtype=np.float32)
+        _check(_lib.qs_mlp_get_grads(self.h, flat.ctypes.data), "mlp_get_grads")
+        return self._split(flat)
+
+    def forward(self, X):
+        """X: float32 device tensor [B][in] -> device tensor [B][out]."""
+        import torch
+        Y = torch.empty((X.shape[0], self.shape[2]), dtype=torch.float32, device=X.device)
+        _check(_lib.qs_mlp_forward(self.h, X.data_ptr(), X.shape[0], Y.data_ptr()), "mlp_forward")
+        return Y
+
+    def train_step(self, X, T, lr):
+        loss = ctypes.c_float(0)
+        _check(_lib.qs_mlp_train_step(self.h, X.data_ptr(), T.data_ptr(), X.shape[0], float(lr),
+                                      ctypes.byref(loss)), "mlp_train_step")
+        return loss.value
+
+    def close(self):
+        if self.h is not None:
+            _lib.qs_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernel_launches():
