@@ -207,11 +207,25 @@ QS_API int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts *op
  * ------------------------------------------------------------------------- */
 #define QS_TRACE_MAX 1024
 
+#define QS_WINDOW 24   /* eigenvalues per mass in the step model's features / traces */
+
+struct qs_mlp;
 typedef struct {
     double c;          /* step factor of step A, slightly below 2 */
     double m0_max;     /* step A stops above it; <= 0 selects 3 (c_sw + c_sw,U(1)) */
     int max_steps;     /* cap on masses visited */
     qs_eig_opts eig;   /* low-mode solver options (warm starts between masses) */
+    /* optional learned step (NULL: the fixed rule).  Network with 8 * QS_WINDOW inputs:
+     * the windows of the last 8 step-A masses (newest first, QS_WINDOW signed Ritz
+     * values each in the solver's order, divided by the newest lambda_bar, zero where
+     * missing); output 0 = log(dm / lambda_bar).  The proposal (clamped to
+     * [lambda_bar / 2, 8 lambda_bar]) replaces c lambda_bar and is accepted only if the
+     * step passes the same no-crossing certificate; otherwise step A falls back to the
+     * edge of the crossing-free interval. */
+    struct qs_mlp *step_model;
+    /* optional HOST buffer of max_steps * QS_WINDOW doubles: the window of every mass
+     * visited, in visiting order (training data for the step model), or NULL */
+    double *window_trace;
 } qs_sign_opts;
 
 typedef struct {
@@ -225,6 +239,7 @@ typedef struct {
     int64_t dslash_f32, dslash_f64;
     int64_t cg_iterations;
     double seconds;
+    int learned_accepted, learned_rejected;   /* step-model proposals certified / not */
     int fail_reason;   /* 0 ok; 1 an eigensolve missed its tolerance; 2 step B found no
                           spectral gap; 3 a step-B count was not certified (bounds straddle
                           the gap, or the window does not reach above it); 4 odd change of

@@ -54,9 +54,13 @@ class EigStats(ctypes.Structure):
 QS_TRACE_MAX = 1024
 
 
+QS_WINDOW = 24
+
+
 class SignOpts(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("m0_max", ctypes.c_double), ("max_steps", ctypes.c_int),
-                ("eig", EigOpts)]
+                ("eig", EigOpts), ("step_model", ctypes.c_void_p),
+                ("window_trace", ctypes.POINTER(ctypes.c_double))]
 
 
 class SignReport(ctypes.Structure):
@@ -66,6 +70,7 @@ class SignReport(ctypes.Structure):
                 ("steps_a", ctypes.c_int), ("steps_b", ctypes.c_int),
                 ("dslash_f32", ctypes.c_int64), ("dslash_f64", ctypes.c_int64),
                 ("cg_iterations", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("learned_accepted", ctypes.c_int), ("learned_rejected", ctypes.c_int),
                 ("fail_reason", ctypes.c_int)]
 
     def as_dict(self):
@@ -75,6 +80,7 @@ class SignReport(ctypes.Structure):
                 "crossings": self.crossings, "steps_a": self.steps_a, "steps_b": self.steps_b,
                 "dslash_f32": self.dslash_f32, "dslash_f64": self.dslash_f64,
                 "cg_iterations": self.cg_iterations, "seconds": self.seconds,
+                "learned_accepted": self.learned_accepted, "learned_rejected": self.learned_rejected,
                 "fail_reason": self.fail_reason}
 
 
@@ -235,9 +241,17 @@ def lowmodes_at_mass(h, m0, opts=None, evecs=None, allow_noconv=False):
     return ev, rs, stats
 
 
-def pfaffian_sign(h, m0_target, opts=None):
-    """qs_pfaffian_sign: returns (sign, report dict)."""
+def pfaffian_sign(h, m0_target, opts=None, step_model=None, trace=False):
+    """qs_pfaffian_sign: returns (sign, report dict).  step_model: an MLP (learned
+    step); trace=True adds report["windows"] (masses visited x QS_WINDOW)."""
     o = opts if opts is not None else sign_default_opts()
+    o.step_model = None if step_model is None else step_model.h
+    buf = None
+    if trace:
+        buf = np.zeros(o.max_steps * QS_WINDOW)
+        o.window_trace = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    else:
+        o.window_trace = None
     sg = ctypes.c_int(0)
     rep = SignReport()
     code = _lib.qs_pfaffian_sign(h, float(m0_target), ctypes.byref(o), ctypes.byref(sg), ctypes.byref(rep))
@@ -245,7 +259,10 @@ def pfaffian_sign(h, m0_target, opts=None):
         err = QStarError(code, "pfaffian_sign")
         err.report = rep.as_dict()
         raise err
-    return sg.value, rep.as_dict()
+    out = rep.as_dict()
+    if trace:
+        out["windows"] = buf[:min(rep.n, o.max_steps) * QS_WINDOW].reshape(-1, QS_WINDOW).copy()
+    return sg.value, out
 
 
 def apply_Q_norm2_noalloc(h, m0, inp, out, norm2):
@@ -378,8 +395,8 @@ class Lattice:
     def lowmodes_at_mass(self, m0, opts=None, evecs=None, allow_noconv=False):
         return lowmodes_at_mass(self.h, m0, opts, evecs, allow_noconv)
 
-    def pfaffian_sign(self, m0_target, opts=None):
-        return pfaffian_sign(self.h, m0_target, opts)
+    def pfaffian_sign(self, m0_target, opts=None, step_model=None, trace=False):
+        return pfaffian_sign(self.h, m0_target, opts, step_model, trace)
 
     def set_profiling(self, on):
         set_profiling(self.h, on)

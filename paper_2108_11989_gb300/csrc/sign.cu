@@ -23,6 +23,7 @@
 #include <time.h>
 
 #include <algorithm>
+#include <vector>
 
 
 extern "C" void qs_sign_default_opts(qs_sign_opts *o)
@@ -39,8 +40,14 @@ extern "C" void qs_sign_default_opts(qs_sign_opts *o)
 
 namespace {
 
+struct Window {
+    double v[QS_WINDOW];
+};
+
 struct Flow {
     int nb;            // step-B prefix size (values that must converge)
+    std::vector<Window> hist;   // windows of the step-A masses, oldest first
+    float *dX, *dY;    // device buffers of the step model (features, outputs)
     qs_lattice *lat;
     qs_sign_opts o;
     qs_sign_report *rep;
@@ -83,10 +90,40 @@ int modes(Flow &f, double m, char phase, Ritz *rz)
         r->resid[r->n] = rz->res[0];
         r->phase[r->n] = phase;
     }
+    if (f.o.window_trace && r->n < f.o.max_steps)
+        for (int i = 0; i < QS_WINDOW; ++i)
+            f.o.window_trace[(size_t)r->n * QS_WINDOW + i] = i < e.k ? rz->theta[i] : 0.0;
     r->n++;
     if (phase == 'A') r->steps_a++; else r->steps_b++;
     if (!conv) r->fail_reason = 1;
     return conv ? QS_OK : QS_ENOCONV;
+}
+
+Window window_of(const Ritz &rz, int k)
+{
+    Window w;
+    for (int i = 0; i < QS_WINDOW; ++i) w.v[i] = i < k ? rz.theta[i] : 0.0;
+    return w;
+}
+
+// dm proposed by the step model from the last 8 step-A windows (newest first,
+// divided by the newest lambda_bar), clamped to [lb / 2, 8 lb]
+int propose(Flow &f, double lb, double *dm)
+{
+    float x[8 * QS_WINDOW];
+    int nh = (int)f.hist.size();
+    for (int j = 0; j < 8; ++j)
+        for (int i = 0; i < QS_WINDOW; ++i)
+            x[j * QS_WINDOW + i] = j < nh ? (float)(f.hist[nh - 1 - j].v[i] / lb) : 0.f;
+    cudaStream_t st = f.lat->stream;
+    QS_CUDA(cudaMemcpyAsync(f.dX, x, sizeof(x), cudaMemcpyHostToDevice, st));
+    QS_TRY(qs_mlp_forward(f.o.step_model, f.dX, 1, f.dY));
+    float y0 = 0.f;
+    QS_CUDA(cudaMemcpyAsync(&y0, f.dY, sizeof(float), cudaMemcpyDeviceToHost, st));
+    QS_CUDA(cudaStreamSynchronize(st));
+    double ly = std::min(std::max((double)y0, log(0.5)), log(8.0));
+    *dm = lb * exp(ly);
+    return QS_OK;
 }
 
 }  // namespace
@@ -106,11 +143,21 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
     f.rep = rep;
     f.steps = 0;
     f.nb = 2;
+    f.dX = f.dY = nullptr;
+    if (f.o.step_model) {
+        if (cudaMalloc(&f.dX, 8 * QS_WINDOW * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&f.dY, 64 * sizeof(float)) != cudaSuccess) {
+            cudaFree(f.dX);
+            return QS_ENOMEM;
+        }
+    }
     f.t0 = now_s();
     const double m0max = f.o.m0_max > 0 ? f.o.m0_max : 3.0 * (lat->csw_su3 + lat->csw_u1);
     int st;
     auto finish = [&](int status) {
         rep->seconds = now_s() - f.t0;
+        cudaFree(f.dX);
+        cudaFree(f.dY);
         return status;
     };
 
@@ -132,13 +179,24 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
                 *sign = (flips % 2 == 0) ? 1 : -1;
                 return finish(QS_OK);
             }
+            f.hist.push_back(window_of(cur, f.o.eig.k));
             double mn = m + f.o.c * lb;              // step 5
+            bool learned = false;
+            if (f.o.step_model) {
+                double dm = 0;
+                st = propose(f, lb, &dm);
+                if (st != QS_OK) return finish(st);
+                mn = m + dm;
+                learned = true;
+            }
             Ritz nw;
             st = modes(f, mn, 'A', &nw);
             if (st != QS_OK) return finish(st);
             ++f.steps;
             double lb2 = fabs(nw.theta[0]), rb2 = nw.res[0];
-            if ((lb - rb) + (lb2 - rb2) < (mn - m)) {
+            bool certified = (lb - rb) + (lb2 - rb2) >= (mn - m);
+            if (learned) { if (certified) rep->learned_accepted++; else rep->learned_rejected++; }
+            if (!certified) {
                 // the step left part of [m, mn] outside both crossing-free intervals:
                 // retreat to the edge of the one around m
                 mn = m + 0.95 * (lb - rb);
