@@ -253,6 +253,24 @@ def run_sign(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_plain:
+        # mixed (FP32 filter + mixed CG + FP64 Rayleigh-Ritz) vs plain FP64 form of the
+        # eigensolver on the same GPU, one cold solve each at equal eigenvalue tolerance
+        cmp = {}
+        for name, prec in (("mixed", 1), ("plain_fp64", 0)):
+            eo = qs.eig_default_opts(k=16, nwant=2, tol=1e-8, cheb_degree=args.degree, warm_start=0,
+                                     max_iter=400, precision=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev, rs, st = lat.lowmodes_at_mass(m0, eo, allow_noconv=True)
+            torch.cuda.synchronize()
+            cmp[name] = {"s": time.perf_counter() - t0, "lambda_bar": abs(float(ev[0])),
+                         "resid": float(rs[0]), "status": st["status"], "passes": st["iterations"],
+                         "dslash_f32": st["dslash_f32"], "dslash_f64": st["dslash_f64"]}
+        cmp["speedup_mixed_over_plain"] = cmp["plain_fp64"]["s"] / cmp["mixed"]["s"]
+        cmp["lambda_bar_rel_diff"] = abs(cmp["mixed"]["lambda_bar"] - cmp["plain_fp64"]["lambda_bar"]) / \
+            cmp["plain_fp64"]["lambda_bar"]
+        out["eigensolve_mixed_vs_plain_fp64"] = cmp
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, m0)
     if rank == 0:
@@ -277,6 +295,7 @@ def main():
     ap.add_argument("--tiled", action="store_true", help="--op-only with the solver's site-tiled layout")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the mixed vs plain FP64 eigensolve")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -376,6 +395,24 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    if not args.no_plain:
+        # mixed (FP32 filter + mixed CG + FP64 Rayleigh-Ritz) vs plain FP64 form of the
+        # eigensolver on the same GPU, one cold solve each at equal eigenvalue tolerance
+        cmp = {}
+        for name, prec in (("mixed", 1), ("plain_fp64", 0)):
+            eo = qs.eig_default_opts(k=16, nwant=2, tol=1e-8, cheb_degree=args.degree, warm_start=0,
+                                     max_iter=400, precision=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev, rs, st = lat.lowmodes_at_mass(m0, eo, allow_noconv=True)
+            torch.cuda.synchronize()
+            cmp[name] = {"s": time.perf_counter() - t0, "lambda_bar": abs(float(ev[0])),
+                         "resid": float(rs[0]), "status": st["status"], "passes": st["iterations"],
+                         "dslash_f32": st["dslash_f32"], "dslash_f64": st["dslash_f64"]}
+        cmp["speedup_mixed_over_plain"] = cmp["plain_fp64"]["s"] / cmp["mixed"]["s"]
+        cmp["lambda_bar_rel_diff"] = abs(cmp["mixed"]["lambda_bar"] - cmp["plain_fp64"]["lambda_bar"]) / \
+            cmp["plain_fp64"]["lambda_bar"]
+        out["eigensolve_mixed_vs_plain_fp64"] = cmp
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, m0)
     if rank == 0:

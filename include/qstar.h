@@ -167,6 +167,9 @@ typedef struct {
     int cheb_degree;   /* degree of the Q^2 Chebyshev filter (>= 2) */
     int warm_start;    /* 1: start from the subspace the handle kept from its last call */
     uint64_t seed;     /* seed of the random start block */
+    int precision;     /* QS_F32: mixed form (FP32 filter, FP32-inner CG refinement, FP64
+                          Rayleigh-Ritz); QS_F64: plain FP64 form (FP64 filter passes and
+                          FP64 Rayleigh-Ritz only) */
 } qs_eig_opts;
 
 typedef struct {
@@ -178,7 +181,7 @@ typedef struct {
 } qs_eig_stats;
 
 /* Fill *opts with defaults (k = 16, nwant = 4, tol = 1e-8, max_iter = 200,
- * cheb_degree = 24, warm_start = 1, seed = 1). */
+ * cheb_degree = 24, warm_start = 1, seed = 1, precision = QS_F32). */
 QS_API void qs_eig_default_opts(qs_eig_opts *opts);
 
 /* Lowest-|lambda| eigenpairs of Q(m0) on the handle's gauge field.

@@ -42,7 +42,7 @@ class BatchItem(ctypes.Structure):
 class EigOpts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nwant", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("warm_start", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int)]
 
 
 class EigStats(ctypes.Structure):

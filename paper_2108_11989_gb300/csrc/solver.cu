@@ -218,6 +218,30 @@ static int cheb_filter(qs_lattice *lat, Workspace *w, double m0, int k, int d, d
     return QS_OK;
 }
 
+// The same filter in FP64 on blk64[0] (V, kept) with blk64[1..5] as work blocks;
+// the filtered block ends in blk64[0] (plain FP64 form of the solver).
+static int cheb_filter64(qs_lattice *lat, Workspace *w, double m0, int k, int d, double a, double b)
+{
+    cudaStream_t st = lat->stream;
+    double *X = w->blk64[1], *Y = w->blk64[2], *Yn = w->blk64[3], *T = w->blk64[4], *AY = w->blk64[5];
+    int64_t n = (int64_t)k * w->nr;
+    CK(cudaMemcpyAsync(X, w->blk64[0], n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    double sigma1 = e / (0.0 - c);
+    double sigma = sigma1, g = 2.0 / sigma1;
+    QS_TRY(opQ2(lat, w, QS_F64, m0, X, T, AY, k));
+    CK(qs_cheb_step<double>(Y, AY, X, X, c, sigma1 / e, 0.0, n, st));
+    for (int i = 2; i <= d; ++i) {
+        double s2 = 1.0 / (g - sigma);
+        QS_TRY(opQ2(lat, w, QS_F64, m0, Y, T, AY, k));
+        CK(qs_cheb_step<double>(Yn, AY, Y, X, c, 2.0 * s2 / e, sigma * s2, n, st));
+        double *tmp = X; X = Y; Y = Yn; Yn = tmp;
+        sigma = s2;
+    }
+    CK(cudaMemcpyAsync(w->blk64[0], Y, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return QS_OK;
+}
+
 // FP32 CG on Q^2 for k right-hand sides in r (overwritten); solution in x.
 static int cg_f32(qs_lattice *lat, Workspace *w, double m0, int k, float *x, float *r, float *p, float *t,
                   float *ap, double tol, int maxit, int *iters)
@@ -305,6 +329,7 @@ extern "C" void qs_eig_default_opts(qs_eig_opts *o)
     o->cheb_degree = 24;
     o->warm_start = 1;
     o->seed = 1;
+    o->precision = QS_F32;
 }
 
 
@@ -320,8 +345,9 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         CK(qs_fill_gauss(w->blk64[0], (int64_t)k * w->nr, o->seed * 0x9E3779B97F4A7C15ULL + 17, st));
     }
     w->have_V = 0;
-    QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, 1));
-    QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F32));
+    const bool plain = o->precision == QS_F64;
+    QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : 1));
+    QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, plain ? QS_F64 : QS_F32));
     // b >= lambda_max(Q^2): ||Q|| = ||D|| <= max_x ||4 + m0 + A(x)|| + ||hopping||,
     // ||hopping|| <= 4 (each direction is a partial isometry pair of norm 1)
     double qn = fabs(4.0 + m0) + lat->clov_norm + 4.0;
@@ -330,7 +356,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
     *conv = 0;
     double prev_worst = 1e300;
     int stall = 0, fstall = 0, restarts = 0;
-    int last_prec = QS_F32;
+    int last_prec = plain ? QS_F64 : QS_F32;
     for (it = 0; it < o->max_iter; ++it) {
         double worst = 0;
         for (int i = 0; i < o->nwant; ++i)
@@ -340,6 +366,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         // depend on how small lambda_bar is.  The FP32 filter cannot improve a block
         // below ~1e-5 relative residual, so only a stagnating refinement hands back.
         bool refine = (worst < 1e-3 || fstall >= 2) && !(stall >= 3 && worst > 1e-5);
+        if (plain) refine = false;   // plain FP64 form: filter passes only
         if (stall >= 3 && fstall >= 2 && restarts < 3) {
             // both stages stagnate (typically a warm start from a distant mass): keep the
             // converged pairs, moved to the front so Cholesky-QR preserves them, and
@@ -356,9 +383,9 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             std::swap(w->blk64[0], w->blk64[2]);
             CK(qs_fill_gauss(w->blk64[0] + (size_t)nconv * w->nr, (int64_t)(k - nconv) * w->nr,
                              o->seed * 0x2545F4914F6CDD1DULL + 977 * (restarts + 1), st));
-            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, 1));
-            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F32));
-            last_prec = QS_F32;
+            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : 1));
+            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, plain ? QS_F64 : QS_F32));
+            last_prec = plain ? QS_F64 : QS_F32;
             stall = fstall = 0;
             prev_worst = 1e300;
             ++restarts;
@@ -381,12 +408,16 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             // Chebyshev filter on [a, b], a = largest Q^2 Ritz value of the block
             double a = rz->mu_max;
             if (a >= 0.5 * b || it == 0) a = std::min(a, 0.05 * b);
-            CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
-            float *Y = nullptr;
-            QS_TRY(cheb_filter(lat, w, m0, k, std::max(2, o->cheb_degree), a, b, &Y));
-            CK(cudaMemsetAsync(w->blk64[2], 0, (size_t)k * w->nr * sizeof(double), st));
-            CK(qs_axpy_f2d(w->blk64[2], Y, DS(w, S_ONES), k, w->nr, st));
-            std::swap(w->blk64[0], w->blk64[2]);
+            if (plain) {
+                QS_TRY(cheb_filter64(lat, w, m0, k, std::max(2, o->cheb_degree), a, b));
+            } else {
+                CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
+                float *Y = nullptr;
+                QS_TRY(cheb_filter(lat, w, m0, k, std::max(2, o->cheb_degree), a, b, &Y));
+                CK(cudaMemsetAsync(w->blk64[2], 0, (size_t)k * w->nr * sizeof(double), st));
+                CK(qs_axpy_f2d(w->blk64[2], Y, DS(w, S_ONES), k, w->nr, st));
+                std::swap(w->blk64[0], w->blk64[2]);
+            }
             ++nf;
         } else {
             // power step with Q^-2: X = Q^-2 V, started from V_i / <v_i, Q^2 v_i>
@@ -407,7 +438,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         }
         // FP32 operator, Gram and rotation while the block is far from converged (its
         // residuals are then far above FP32 rounding); FP64 from the refinement on
-        last_prec = (refine || worst < 1e-3) ? QS_F64 : QS_F32;
+        last_prec = (plain || refine || worst < 1e-3) ? QS_F64 : QS_F32;
         QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, last_prec == QS_F32));
         QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, last_prec));
         double nw = 0;
@@ -438,7 +469,7 @@ extern "C" int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts
     qs_eig_opts o;
     if (opts) o = *opts; else qs_eig_default_opts(&o);
     if (o.k < 2 || o.k > 64 || (o.k & 1) || o.nwant < 1 || o.nwant > o.k || !(o.tol > 0) || o.max_iter < 0 ||
-        o.cheb_degree < 2)
+        o.cheb_degree < 2 || (o.precision != QS_F32 && o.precision != QS_F64))
         return QS_EINVAL;
     if (12 * lat->g.Ns < o.k) return QS_EINVAL;
     CK(cudaSetDevice(lat->device));

@@ -86,3 +86,16 @@ def test_eigenvectors_returned(qs):
         assert np.linalg.norm(r) <= 1e-8 * abs(ev[i]) + 1e-12
         assert abs(np.linalg.norm(v[i]) - 1) < 1e-12
     lat.close()
+
+
+def test_plain_fp64_form_matches(qs):
+    """precision = QS_F64 (FP64 filter and Rayleigh-Ritz only) gives the same low
+    eigenvalues as the dense oracle."""
+    cfg = make_config(T=4, L=2, eps=0.9, theta_sigma=0.4, csw_su3=1.3, csw_u1=0.8, seed=5)
+    lat = lattice(qs, cfg)
+    opts = qs.eig_default_opts(k=16, nwant=8, tol=1e-9, cheb_degree=16, precision=0, max_iter=400)
+    ev, rs, st = lat.lowmodes_at_mass(-0.6, opts)
+    ref = np.linalg.eigvalsh(WilsonDirac(cfg).dense_Q(-0.6))
+    check_against(ev, rs, ref, 8)
+    assert st["dslash_f32"] == 0 and st["refine_passes"] == 0
+    lat.close()
