@@ -98,9 +98,10 @@ __global__ void __launch_bounds__(256) gram_part(const double *__restrict__ A, i
                                                  const double *__restrict__ B, int kb, int64_t nc,
                                                  double *part)
 {
+    // FP64 staging: double2 [ka + kb][GCH]; FP32 staging (LOWP): float2, converted once
+    // per element when loaded (FP64 -> FP32 conversions run on the FP64 pipe)
     extern __shared__ double2 gsh[];
-    double2 *sa = gsh;               // [ka][GCH]
-    double2 *sb = gsh + ka * GCH;    // [kb][GCH]
+    float2 *gsf = reinterpret_cast<float2 *>(gsh);
     const double2 *A2 = reinterpret_cast<const double2 *>(A);
     const double2 *B2 = reinterpret_cast<const double2 *>(B);
     const int P = ka * kb;
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(256) gram_part(const double *__restrict__ A, i
             int64_t idx = e0 + e;
             double2 val = make_double2(0, 0);
             if (idx < nc) val = v < ka ? A2[(int64_t)v * nc + idx] : B2[(int64_t)(v - ka) * nc + idx];
-            gsh[t] = val;
+            if (LOWP) gsf[t] = make_float2((float)val.x, (float)val.y);
+            else gsh[t] = val;
         }
         __syncthreads();
 #pragma unroll
@@ -124,18 +126,18 @@ __global__ void __launch_bounds__(256) gram_part(const double *__restrict__ A, i
             int q = threadIdx.x + 256 * m;
             if (q < P) {
                 int i = q / kb, j = q % kb;
-                const double2 *x = sa + i * GCH, *y = sb + j * GCH;
                 if (LOWP) {
+                    const float2 *x = gsf + i * GCH, *y = gsf + (ka + j) * GCH;
                     float re = 0.f, im = 0.f;
 #pragma unroll 8
                     for (int e = 0; e < GCH; ++e) {
-                        double2 u = x[e], w = y[e];
-                        float ux = (float)u.x, uy = (float)u.y, wx = (float)w.x, wy = (float)w.y;
-                        re = fmaf(ux, wx, fmaf(uy, wy, re));
-                        im = fmaf(ux, wy, fmaf(-uy, wx, im));
+                        float2 u = x[e], w = y[e];
+                        re = fmaf(u.x, w.x, fmaf(u.y, w.y, re));
+                        im = fmaf(u.x, w.y, fmaf(-u.y, w.x, im));
                     }
                     ar[m] += re; ai[m] += im;
                 } else {
+                    const double2 *x = gsh + i * GCH, *y = gsh + (ka + j) * GCH;
                     double re = ar[m], im = ai[m];
 #pragma unroll 8
                     for (int e = 0; e < GCH; ++e) {
@@ -164,7 +166,11 @@ __global__ void rotate_kernel(const double *__restrict__ W, int ka, const double
                               int64_t nc, double *__restrict__ V)
 {
     extern __shared__ double2 csh[];
-    for (int t = threadIdx.x; t < ka * kc; t += blockDim.x) csh[t] = C[t];
+    float2 *csf = reinterpret_cast<float2 *>(csh);
+    for (int t = threadIdx.x; t < ka * kc; t += blockDim.x) {
+        if (LOWP) csf[t] = make_float2((float)C[t].x, (float)C[t].y);
+        else csh[t] = C[t];
+    }
     __syncthreads();
     const double2 *W2 = reinterpret_cast<const double2 *>(W);
     double2 *V2 = reinterpret_cast<double2 *>(V);
@@ -180,8 +186,9 @@ __global__ void rotate_kernel(const double *__restrict__ W, int ka, const double
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
                     if (j0 + jj < kc) {
-                        double2 c = csh[i * kc + j0 + jj];
-                        T cx = (T)c.x, cy = (T)c.y;
+                        T cx, cy;
+                        if (LOWP) { float2 c = csf[i * kc + j0 + jj]; cx = c.x; cy = c.y; }
+                        else { double2 c = csh[i * kc + j0 + jj]; cx = (T)c.x; cy = (T)c.y; }
                         re[jj] = wx * cx - wy * cy + re[jj];
                         im[jj] = wx * cy + wy * cx + im[jj];
                     }
