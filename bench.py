@@ -42,6 +42,28 @@ def reals_per_site(nrhs):
     return 48 * nrhs + 72
 
 
+def kernel_source_hash():
+    """sha256 of the sources the operator kernel is compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dslash.cu", "dslash.cuh", "qs_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2108_11989_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(nrhs):
+    """DRAM bytes per launch of the FP32 operator from the last ncu capture, if that
+    capture was of the current kernel source and the same nrhs; else None."""
+    p = os.path.join(ROOT, "profiles", "dslash_f32_tiled_16x16x16x32.traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_sha256") != kernel_source_hash() or d.get("nrhs") != nrhs:
+        return None
+    return d["dram_bytes_per_launch"]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -244,7 +266,8 @@ def run_sign(args):
                     "f32_operator_share_of_step": f32["ms"] / total_ms if total_ms > 0 else None,
                     "f64_operator_ms_per_step": prof["f64"]["ms"] / args.steps},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "dslash_kernel<float>",
+                     "frac": achieved / peak, "traffic": measured_traffic(args.k),
+                     "kernel": "dslash_kernel<float>",
                      "launches": f32["launches"], "avg_launch_us": 1e3 * f32["ms"] / max(1, f32["launches"]),
                      "peak_source": f"{src} hbm_gbs",
                      "bytes_model": "(48 nrhs + 72) reals/site x 4 B per launch"},
