@@ -30,7 +30,6 @@ struct Workspace {
     int *di;              // device ints, 64 + 8
     double *hp;           // pinned host mirror of ds (S_NSLOT x 64)
     int *hi;              // pinned host ints (64 + 8)
-    int vi;               // index of the block holding the current subspace V
     int have_V;
     int64_t f32_count, f64_count, cg_count;
 };
@@ -65,14 +64,8 @@ void qs_free_workspace(qs_lattice *lat)
         }                                                                  \
     } while (0)
 
-static int ws_get(qs_lattice *lat, int k, Workspace **out)
+static int ws_alloc(qs_lattice *lat, Workspace *w, int k)
 {
-    Workspace *w = lat->ws;
-    if (w && w->k == k) { *out = w; return QS_OK; }
-    qs_free_workspace(lat);
-    w = (Workspace *)calloc(1, sizeof(Workspace));
-    if (!w) return QS_ENOMEM;
-    lat->ws = w;
     w->k = k;
     w->nr = lat->g.Ns * 24;
     size_t n64 = (size_t)k * w->nr * sizeof(double), n32 = (size_t)k * w->nr * sizeof(float);
@@ -91,8 +84,24 @@ static int ws_get(qs_lattice *lat, int k, Workspace **out)
     for (int i = 0; i < 64; ++i) w->hp[i] = 1.0;
     CK(cudaMemcpyAsync(DS(w, S_ONES), w->hp, 64 * sizeof(double), cudaMemcpyHostToDevice, lat->stream));
     CK(cudaStreamSynchronize(lat->stream));
-    w->vi = 0;
     w->have_V = 0;
+    return QS_OK;
+}
+
+// the handle's workspace for block size k: allocated all at once, or not at all
+static int ws_get(qs_lattice *lat, int k, Workspace **out)
+{
+    Workspace *w = lat->ws;
+    if (w && w->k == k) { *out = w; return QS_OK; }
+    qs_free_workspace(lat);
+    w = (Workspace *)calloc(1, sizeof(Workspace));
+    if (!w) return QS_ENOMEM;
+    int st = ws_alloc(lat, w, k);
+    if (st != QS_OK) {
+        ws_free(w);
+        return st;
+    }
+    lat->ws = w;
     *out = w;
     return QS_OK;
 }
