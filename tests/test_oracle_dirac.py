@@ -183,3 +183,17 @@ def test_lazy_site_blocks_match_full_assembly():
     b = lazy.apply_Q(psi, -0.2, sites)
     assert np.allclose(a, b, atol=1e-14)
     assert np.allclose(full.sparse_Q(-0.2) @ psi, full.apply_Q(psi, -0.2), atol=1e-13)
+
+
+def test_pfaffian_squared_is_det_D():
+    """pf[C T D]^2 = det D (Sec. 3): with pf^2 = det for the antisymmetric C T D this
+    needs det(C T) = 1 for the doubled-lattice C and T."""
+    from oracle.pfaffian import pfaffian
+    op = WilsonDirac(rough_cfg(T=2, L=2, seed=4))
+    m0 = -0.35
+    la, ph = pfaffian(op.dense_CTD(m0))
+    sd, ld = np.linalg.slogdet(op.dense_D(m0))
+    assert np.isclose(2 * la, ld, atol=1e-9)
+    assert np.isclose(ph * ph, sd, atol=1e-9)
+    sct, lct = np.linalg.slogdet(op.CT_matrix().toarray())
+    assert np.isclose(lct, 0.0, atol=1e-12) and np.isclose(sct, 1.0)
