@@ -57,7 +57,14 @@ enum qs_status {
     QS_EUNDECIDED = -7   /* |lambda| at the target mass is below its certified accuracy */
 };
 
-enum qs_prec { QS_F64 = 0, QS_F32 = 1 };
+/* Precision of the spinors given to the operator calls.  QS_F64: double, FP64
+ * arithmetic.  QS_F32: float, FP32 arithmetic.  QS_F16 / QS_BF16: 16-bit storage with
+ * FP32 arithmetic, in the tiled layout only (OR QS_LAYOUT_TILED into prec): tiles of 16
+ * sites, each 12 x 16 words of two 16-bit reals (re, im of component c of site
+ * 16 t + j at word 16 c + j) followed by 16 FP32 scales, 832 bytes per tile; site j's 24
+ * reals are stored divided by its scale (the largest of their magnitudes), so a
+ * vector takes 52 bytes per site.  Outputs are written in the same format. */
+enum qs_prec { QS_F64 = 0, QS_F32 = 1, QS_F16 = 2, QS_BF16 = 3 };
 
 /* OR into the prec argument of qs_apply_Dw / qs_apply_Q to pass spinors in the
  * solver's site-tiled layout [rhs][site / 16][spin-colour 12][site % 16][re, im]
@@ -86,19 +93,33 @@ QS_API int64_t qs_n_sites(const qs_lattice *lat);
 /* Load a gauge configuration (Sec. 2: SU(3) x U(1) links, c_sw's) from HOST arrays
  * (layouts above; copied, the caller keeps ownership), build the doubled links and
  * the SW term A(x) on the GPU in FP64, and keep FP64 and FP32 copies resident.
- * Replaces any earlier configuration of the handle.  Synchronises the stream. */
+ * Replaces any earlier configuration of the handle.  Synchronises the stream.
+ * Returns QS_ENUMERIC (and leaves no field loaded) if a link, an angle or the SW
+ * term built from them is NaN or infinite. */
 QS_API int qs_load_gauge(qs_lattice *lat, const double *su3, const double *u1_theta,
                   double csw_su3, double csw_u1);
 
-/* out = D(m0) in for nrhs vectors (Sec. 2 operator on the doubled lattice, Sec. 3).
- * in, out: device buffers of nrhs * N_s * 24 reals, canonical layout (or the tiled one
- * with QS_LAYOUT_TILED), in precision prec (QS_F64: double, arithmetic in FP64; QS_F32:
- * float, arithmetic in FP32).
- * Asynchronous on the handle's stream. */
+/* out = D(m0) in for nrhs <= 64 vectors (Sec. 2 operator on the doubled lattice, Sec. 3).
+ * in, out: device buffers of nrhs vectors, canonical layout (or the tiled one with
+ * QS_LAYOUT_TILED), in precision prec (QS_F64: double, arithmetic in FP64; QS_F32:
+ * float, arithmetic in FP32; QS_F16 / QS_BF16: tiled 16-bit storage, arithmetic in
+ * FP32, see enum qs_prec).  Vectors are contiguous: N_s * 24 reals each, or N_s * 52
+ * bytes in 16-bit storage; 16-byte aligned.  Asynchronous on the handle's stream.
+ * The first call for a (precision, layout, nrhs) on a lattice shape times the launch
+ * variants of the kernel once on the stream (writing only `out`); if the environment
+ * variable QS_TUNE_CACHE names a file, choices are read from it and new ones appended,
+ * so later processes on the same GPU model skip the timing. */
 QS_API int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec);
 
 /* out = Q(m0) in = gamma_5 D(m0) in (Sec. 3).  Same arguments as qs_apply_Dw. */
 QS_API int qs_apply_Q(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec);
+
+/* Convert nrhs spinors between precisions, both in the tiled layout (in_prec, out_prec:
+ * QS_F64, QS_F32, QS_F16, QS_BF16, different; QS_LAYOUT_TILED may be ORed in).  Into 16
+ * bits each site is scaled by its largest component; out of 16 bits the values are
+ * expanded exactly.  DEVICE buffers, not overlapping, 16-byte aligned.  Asynchronous
+ * on the handle's stream.  (Storage conversion; no counterpart in the paper.) */
+QS_API int qs_convert_spinors(qs_lattice *lat, const void *in, int in_prec, void *out, int out_prec, int nrhs);
 
 /* Several configurations in ONE launch (the batched form of the hot path: many
  * masses, several gauge configurations of uneven volume, blocks of vectors).
@@ -162,14 +183,18 @@ QS_API int qs_mlp_train_step(qs_mlp *net, const float *X, const float *T, int B,
 typedef struct {
     int k;             /* block size = eigenpairs returned, even, 2..64 */
     int nwant;         /* the nwant smallest |theta| must meet tol (1..k) */
-    double tol;        /* target: r_i <= tol * |theta_i| for i < nwant */
+    double tol;        /* target: r_i <= tol * |theta_i| for i < nwant, or r_i <= 1e-13 qn
+                          (qn = |4 + m0| + max ||A(x)|| + 4 >= ||Q||), so that an exact zero
+                          mode also ends the iteration (with |theta_i| - r_i <= 0) */
     int max_iter;      /* cap on subspace passes (filter + refinement) */
     int cheb_degree;   /* degree of the Q^2 Chebyshev filter (>= 2) */
     int warm_start;    /* 1: start from the subspace the handle kept from its last call */
     uint64_t seed;     /* seed of the random start block */
     int precision;     /* QS_F32: mixed form (FP32 filter, FP32-inner CG refinement, FP64
-                          Rayleigh-Ritz); QS_F64: plain FP64 form (FP64 filter passes and
-                          FP64 Rayleigh-Ritz only) */
+                          Rayleigh-Ritz); QS_F16 / QS_BF16: the mixed form with the filter's
+                          vectors stored in 16 bits (per-site scale, FP32 arithmetic);
+                          QS_F64: plain FP64 form (FP64 filter passes and FP64 Rayleigh-Ritz
+                          only) */
 } qs_eig_opts;
 
 typedef struct {
@@ -199,10 +224,11 @@ QS_API int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts *op
  * W_sgn(m0) = (-1)^(number of zero crossings of eigenvalues of Q between m0 and
  * large mass), counted along the mass flow:
  *  step A (Sec. 3, steps 1-5): m <- m + c lambda_bar while lambda_bar does not
- *    decrease; stop with the sign found so far once m > m0_max.  Each step is
- *    certified by |lambda'| <= 1 (eq. derivativebound) with lower bounds
- *    lambda_bar - r: (lb_n - r_n) + (lb_{n+1} - r_{n+1}) >= m_{n+1} - m_n; a step
- *    that fails it is shortened to m_n + 0.95 (lb_n - r_n).
+ *    decrease; stop with the sign found so far once m > m0_max.  lambda_bar is the
+ *    smallest |theta| of the block and lo = min (|theta_j| - r_j) its certified lower
+ *    bound.  Each step is certified by |lambda'| <= 1 (eq. derivativebound):
+ *    lo_n + lo_{n+1} >= m_{n+1} - m_n; a step that fails it hands over to step B
+ *    from m_n (or, with the retreat option, is shortened to m_n + 0.95 lo_n).
  *  step B (the paper defers it to other work; our reading): from the last
  *    certified mass, step by dm inside a spectral gap (a - dm, a + dm) of the
  *    tracked window and add the change of the number of eigenvalues in (-a, 0);
@@ -221,21 +247,26 @@ typedef struct {
     /* optional learned step (NULL: the fixed rule).  Network with 8 * QS_WINDOW inputs:
      * the windows of the last 8 step-A masses (newest first, QS_WINDOW signed Ritz
      * values each in the solver's order, divided by the newest lambda_bar, zero where
-     * missing); output 0 = log(dm / lambda_bar).  The proposal (clamped to
-     * [lambda_bar / 2, 8 lambda_bar]) replaces c lambda_bar and is accepted only if the
-     * step passes the same no-crossing certificate; otherwise step A falls back to the
-     * edge of the crossing-free interval. */
+     * missing); output 0 = log(dm / lambda_bar).  The proposal, clamped to
+     * [c lambda_bar, 8 lambda_bar] so that it can only lengthen the plain step, replaces
+     * c lambda_bar; the step is then certified exactly as a plain one. */
     struct qs_mlp *step_model;
     /* optional HOST buffer of max_steps * QS_WINDOW doubles: the window of every mass
      * visited, in visiting order (training data for the step model), or NULL */
     double *window_trace;
+    /* 0 (default): the paper's order -- a step-A step that is not certified counts as
+     * step 3 and step B starts from the last certified mass.  1: such a step is first
+     * shortened to m + 0.95 lo (the edge of the crossing-free interval around m). */
+    int retreat;
 } qs_sign_opts;
 
 typedef struct {
     int n;                              /* masses visited */
     double mass[QS_TRACE_MAX];
-    double lambda_bar[QS_TRACE_MAX];    /* min |theta| at that mass */
-    double resid[QS_TRACE_MAX];         /* residual bound of that theta */
+    double lambda_bar[QS_TRACE_MAX];    /* min |theta| at that mass (block values with
+                                           r <= |theta| / 2, and the converged ones) */
+    double resid[QS_TRACE_MAX];         /* lambda_bar minus its certified lower bound
+                                           min (|theta_j| - r_j) over the same values */
     char phase[QS_TRACE_MAX];           /* 'A' or 'B' */
     int crossings;                      /* zero crossings counted by step B */
     int steps_a, steps_b;
@@ -260,11 +291,30 @@ QS_API int qs_pfaffian_sign(qs_lattice *lat, double m0_target, const qs_sign_opt
                             qs_sign_report *report);
 
 /* ---------------------------------------------------------------------------
+ * Even-odd factor of the mass reweighting (Sec. 4).  With even-odd preconditioning the
+ * reweighting factor from bare mass m to m' carries the exact factor
+ *   W_eo = |det[D^oo_m' (D^oo_m)^-1]|^(1/2),
+ * D^oo the operator restricted to the odd sites of the doubled lattice (parity
+ * (t + z + y + x) mod 2).  No hopping term connects two odd sites, so D^oo is the
+ * site-diagonal 4 + m0 + A(x) and its log-determinant is a sum of 6 x 6 block terms.
+ * ------------------------------------------------------------------------- */
+
+/* logdet[i] = sum over odd doubled sites x of log|det(4 + m0[i] + A(x))| (FP64) for
+ * nmass <= 16 masses (host arrays).  Synchronises the stream.  QS_ENUMERIC if a block
+ * is singular (log of zero) or the field is not finite. */
+QS_API int qs_log_det_oo(qs_lattice *lat, int nmass, const double *m0, double *logdet);
+
+/* *w_eo = W_eo(m -> mp) and *log_w_eo its logarithm (either may be NULL, not both). */
+QS_API int qs_w_eo(qs_lattice *lat, double m, double mp, double *w_eo, double *log_w_eo);
+
+/* ---------------------------------------------------------------------------
  * Kernel profiling (measurement support, no counterpart in the paper).  While on,
  * every operator launch of the handle is bracketed by CUDA events on the handle's
  * stream; qs_get_profile synchronises the stream and reports per precision the
  * launches, their summed device time and their algorithmic bytes (per doubled site:
- * 48 spinor reals per right-hand side + 72 link and SW-term reals per launch).
+ * every right-hand side's spinor in and out -- plus two more spinors for the fused
+ * Chebyshev step of the filter -- and once per launch 36 link + 36 SW-term reals, in
+ * the operator's arithmetic precision).
  * ------------------------------------------------------------------------- */
 typedef struct {
     int64_t launches;
@@ -273,7 +323,7 @@ typedef struct {
 } qs_kernel_prof;
 
 typedef struct {
-    qs_kernel_prof dslash[2];   /* [QS_F64], [QS_F32] */
+    qs_kernel_prof dslash[4];   /* by spinor precision [QS_F64], [QS_F32], [QS_F16], [QS_BF16] */
 } qs_profile;
 
 /* on = 1 starts (and zeroes) the counters, on = 0 stops recording. */

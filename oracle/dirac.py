@@ -24,6 +24,8 @@ form with C* momenta), gamma_5-hermiticity, antisymmetry of C T D, the
 degenerate partner C T gamma_5 v^*, gauge covariance, and a closed form of the
 clover term next to a single plaquette carrying flux.
 """
+import ctypes
+
 import numpy as np
 import scipy.sparse as sp
 
@@ -173,6 +175,93 @@ class WilsonDirac:
 
     def dense_CTD(self, m0):
         return (self.CT_matrix() @ self.sparse_D(m0)).toarray()
+
+
+class WilsonDiracC:
+    """The same operator applied by plain C loops (oracle/dirac_c.c, OpenMP), for
+    lattices where the assembled 12 x 12 hopping blocks of ``WilsonDirac`` do not fit
+    in memory.  Holds the doubled links V, the SW blocks A(x) of every site (from
+    ``clover_term``), the neighbour tables and the gamma matrices.
+
+    Pinned by tests/test_oracle_dirac.py: equal to ``WilsonDirac.apply_D`` / ``apply_Q``
+    on rough small lattices (an independent evaluation of the same formula: numpy
+    block assembly there, explicit loops over spin and colour here), the free-field
+    plane-wave closed form, and gamma_5-hermiticity of Q."""
+
+    def __init__(self, cfg):
+        self.cfg = cfg
+        self.lat = DoubledLattice(cfg.T, cfg.L, cfg.cstar_mask, cfg.t_antiperiodic)
+        lat = self.lat
+        U3, theta = lat.doubled_links(cfg.su3, cfg.theta)
+        self.V = np.ascontiguousarray(U3 * np.exp(1j * theta)[:, :, None, None])
+        self.A = np.ascontiguousarray(clover_term(lat, U3, theta, cfg.csw_su3, cfg.csw_u1))
+        ns = lat.n_sites
+        self.fw = np.zeros((4, ns), dtype=np.int64)
+        self.bw = np.zeros((4, ns), dtype=np.int64)
+        self.bcf = np.zeros((4, ns))
+        self.bcb = np.zeros((4, ns))
+        for mu in range(4):
+            (self.fw[mu], self.bcf[mu]), (self.bw[mu], self.bcb[mu]) = lat.neighbour(mu, +1), lat.neighbour(mu, -1)
+        self.gam = np.ascontiguousarray(GAMMA)
+        self.n = 12 * ns
+        self._lib = _load_c()
+
+    def _args(self):
+        P = ctypes.c_void_p
+        return [ctypes.c_long(self.lat.n_sites), P(self.V.ctypes.data), P(self.A.ctypes.data),
+                P(self.fw.ctypes.data), P(self.bw.ctypes.data), P(self.bcf.ctypes.data),
+                P(self.bcb.ctypes.data), P(self.gam.ctypes.data)]
+
+    def apply(self, psi, m0, gamma5):
+        x = np.ascontiguousarray(psi, dtype=np.complex128).reshape(-1)
+        out = np.empty_like(x)
+        self._lib.wd_apply(*self._args(), ctypes.c_double(m0), ctypes.c_int(int(gamma5)),
+                           ctypes.c_void_p(x.ctypes.data), ctypes.c_void_p(out.ctypes.data))
+        return out.reshape(np.shape(psi))
+
+    def apply_D(self, psi, m0):
+        return self.apply(psi, m0, 0)
+
+    def apply_Q(self, psi, m0):
+        return self.apply(psi, m0, 1)
+
+    def residuals(self, vecs, theta, m0):
+        """||Q(m0) v_i - theta_i v_i|| for the rows v_i of vecs [k][n]."""
+        v = np.ascontiguousarray(vecs, dtype=np.complex128)
+        k = v.shape[0]
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        work = np.empty(self.n, dtype=np.complex128)
+        res = np.zeros(k)
+        self._lib.wd_residuals(*self._args(), ctypes.c_double(m0), ctypes.c_int(k), ctypes.c_void_p(v.ctypes.data),
+                               ctypes.c_void_p(th.ctypes.data), ctypes.c_void_p(work.ctypes.data),
+                               ctypes.c_void_p(res.ctypes.data))
+        return res
+
+
+_clib = None
+
+
+def build_c(force=False):
+    """Compile oracle/dirac_c.c into oracle/_build/libwdoracle.so (gcc, OpenMP)."""
+    import os
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    out_dir = os.path.join(here, "_build")
+    so = os.path.join(out_dir, "libwdoracle.so")
+    src = os.path.join(here, "dirac_c.c")
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+        os.makedirs(out_dir, exist_ok=True)
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", src, "-o", so, "-lm"])
+    return so
+
+
+def _load_c():
+    global _clib
+    if _clib is None:
+        _clib = ctypes.CDLL(build_c())
+        _clib.wd_apply.restype = None
+        _clib.wd_residuals.restype = None
+    return _clib
 
 
 def gamma5_vec(psi):

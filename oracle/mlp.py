@@ -10,8 +10,11 @@ Loss over a batch of B rows (T = targets, column 0 a regression target, columns
 Adam (Kingma & Ba, ICLR 2015): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
 p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 
-Pinned by tests/test_oracle_mlp.py: gradients against central finite differences,
-and the first Adam step (which moves every parameter by lr * sign(g) + O(eps)).
+Pinned by tests/test_oracle_mlp.py: the loss against a closed form, gradients
+against central finite differences, the first Adam step (which moves every
+parameter by lr * sign(g) + O(eps)), five steps with a constant gradient (exact bias
+corrections: each moves p by lr g / (|g| + eps)), and two steps on p^2 / 2 against
+values worked out by hand.
 """
 import numpy as np
 

@@ -11,24 +11,33 @@ Three routes, all FP64 on the CPU:
 2. ``sign_by_eigencount``: pf[CTD] = prod_{n=1}^{12V} lambda_n (Sec. 3), one lambda per
    degenerate pair, so W_sgn = (-1)^(N_-/2) with N_- the number of negative
    eigenvalues of the dense Q counted with multiplicity.
-3. ``pfaffian_sign_flow``: the mass-flow algorithm.  Step A as the enumerated
-   algorithm of Sec. 3 (steps 1-5, c slightly below 2), each certification made with
-   lower bounds lambda_bar - ||r||; a step that leaves the crossing-free interval
-   (m - lambda_bar, m + lambda_bar) of eq. derivativebound uncovered is shortened to
-   its edge (m + 0.95 (lambda_bar - r)) instead of being accepted.  Step B is not
-   described in the paper (it cites other work); our reading: from the last
-   certified mass, walk upward in steps dm chosen inside a spectral gap of the
-   tracked window (gap between sorted |lambda|: s_i < a < s_{i+1},
-   dm <= (s_{i+1} - s_i)/2 minus residual margins), and add the change of the number
-   of eigenvalues in (-a, 0).  By |lambda'| <= 1 (eq. derivativebound) no eigenvalue
-   outside (-a, a) can change sign in the step, and the eigenvalues inside stay
-   inside, so the change of N_- is exact.  Return to step A as soon as lambda_bar
-   grows again.  Step 4 also fires when m + (lambda_bar - r) > m0_max: the interval
-   (m - lambda_bar, m + lambda_bar) of eq. derivativebound already covers m0_max.
+3. ``pfaffian_sign_flow``: the mass-flow algorithm.  Step A is the enumerated
+   algorithm of Sec. 3 in its order: (1) m^(0) = m_target; (2) lambda_bar^(n); (3) if
+   lambda_bar^(n) < lambda_bar^(n-1), go to step B; (4) if m^(n) > m0_max, W_sgn is the
+   sign found so far; (5) m^(n+1) = m^(n) + c lambda_bar^(n), c slightly below 2.
+   Finite accuracy: lambda_bar is the smallest |lambda| of the window and
+   lo = min (|lambda_j| - r_j) its certified lower bound; the step m^(n) -> m^(n+1) is
+   covered by the crossing-free intervals of eq. derivativebound iff
+   lo^(n) + lo^(n+1) >= m^(n+1) - m^(n).  With exact eigenvalues that holds whenever
+   lambda_bar does not decrease (c < 2); a step that is not covered is treated as step 3
+   and step B starts from m^(n), the last mass the flow is certified up to; after a
+   covered step where lambda_bar decreased, step B starts from m^(n+1).  Step 4 also
+   fires when m + lo > m0_max (the interval around m already covers m0_max).
+   ``retreat=True`` (an option, not the paper's algorithm): an uncovered step is first
+   shortened to m^(n) + 0.95 lo^(n), the edge of the crossing-free interval around m^(n).
+   Step B is not described in the paper (it cites other work); our reading: from the
+   start mass, walk upward in steps dm chosen inside a spectral gap of the tracked
+   window (gap between sorted |lambda|: s_i < a < s_{i+1}, dm <= (s_{i+1} - s_i)/2 minus
+   residual margins), and add the change of the number of eigenvalues in (-a, 0).  By
+   |lambda'| <= 1 (eq. derivativebound) no eigenvalue outside (-a, a) can change sign in
+   the step, and the eigenvalues inside stay inside, so the change of N_- is exact.
+   Return to step A as soon as lambda_bar grows again.
 
-Pinned by tests/test_oracle_sign.py: routes 1 and 2 agree (the theorem of
-Sec. 3), sign +1 above m0_max, and the flow agrees with both on tiny lattices,
-including configurations with negative signs.
+Pins (tests/test_oracle_sign.py): routes 1 and 2 agree with each other and with
+the real eigenvalues of D(0) (det D(m0) = prod (mu + m0)) on a rough field with
+negative signs (the theorem of Sec. 3); sign +1 above m0_max; the flow, with and
+without the retreat option, reproduces the definition on that field, and its step-A
+trace obeys the paper's rules (steps of exactly c lambda_bar while lambda_bar grows).
 """
 import numpy as np
 
@@ -69,29 +78,30 @@ def sign_by_eigencount(op, m0):
 
 
 def _lambda_bar(modes):
+    """(lambda_bar, lo): the smallest |lambda| and min (|lambda_j| - r_j) of a window."""
     w, r = modes
-    i = int(np.argmin(np.abs(w)))
-    return abs(w[i]), r[i]
+    a = np.abs(np.asarray(w))
+    return float(np.min(a)), float(np.min(a - np.asarray(r)))
 
 
-def pfaffian_sign_flow(modes_fn, m_target, m0_max, c=1.9, max_steps=200, min_step=1e-9):
+def pfaffian_sign_flow(modes_fn, m_target, m0_max, c=1.9, max_steps=200, min_step=1e-9, retreat=False):
     """W_sgn(m_target) by the mass flow.  modes_fn(m) -> (signed eigenvalues of Q(m)
     closest to zero sorted by |lambda|, their residual bounds); it must return the
     k lowest |lambda| with k >= 4.  Returns (sign, report)."""
     report = {"masses": [], "lambda_bar": [], "phase": [], "crossings": 0, "evals": 0}
 
-    def modes(m):
+    def modes(m, phase):
         report["evals"] += 1
         w, r = modes_fn(m)
         report["masses"].append(m)
         report["lambda_bar"].append(float(np.min(np.abs(w))))
+        report["phase"].append(phase)
         return np.asarray(w), np.asarray(r)
 
-    m = m_target
-    cur = modes(m)
-    lb, rb = _lambda_bar(cur)
-    report["phase"].append("A")
-    if lb - rb <= 0:
+    m = m_target                                         # step 1
+    cur = modes(m, "A")                                  # step 2
+    lb, lo = _lambda_bar(cur)
+    if lo <= 0:
         return UNDECIDED, report
     flips = 0          # change of N_- / 2 accumulated by step B (mod 2 decides)
     steps = 0
@@ -99,23 +109,22 @@ def pfaffian_sign_flow(modes_fn, m_target, m0_max, c=1.9, max_steps=200, min_ste
         # ---- step A (steps 1-5 of the enumerated algorithm) ----------------
         go_b = False
         while steps < max_steps:
-            lb, rb = _lambda_bar(cur)
-            if m > m0_max or m + (lb - rb) > m0_max:   # step 4 (or its interval covers m0_max)
+            lb, lo = _lambda_bar(cur)
+            if m > m0_max or m + lo > m0_max:            # step 4 (or its interval covers m0_max)
                 return (1 if flips % 2 == 0 else -1), report
             m_new = m + c * lb                           # step 5
-            new = modes(m_new)
-            report["phase"].append("A")
+            new = modes(m_new, "A")                      # step 2 at n + 1
             steps += 1
-            lb2, rb2 = _lambda_bar(new)
-            covered = (lb - rb) + (lb2 - rb2) >= (m_new - m)
+            lb2, lo2 = _lambda_bar(new)
+            covered = lo + lo2 >= (m_new - m)
             if not covered:
-                # the step went past the interval (m - lb, m + lb) of eq. derivativebound
-                # that is free of crossings: retreat to its edge
-                m_new = m + 0.95 * (lb - rb)
-                new = modes(m_new)
-                report["phase"].append("A")
+                if not retreat:                          # step 3: B from the certified mass m
+                    go_b = True
+                    break
+                m_new = m + 0.95 * lo                    # retreat option
+                new = modes(m_new, "A")
                 steps += 1
-                lb2, rb2 = _lambda_bar(new)
+                lb2, lo2 = _lambda_bar(new)
             m, cur = m_new, new
             if lb2 < lb:                                 # step 3: lambda_bar decreases
                 go_b = True
@@ -140,8 +149,7 @@ def pfaffian_sign_flow(modes_fn, m_target, m0_max, c=1.9, max_steps=200, min_ste
             before = int(np.sum((w < 0) & (np.abs(w) < a)))
             lb_old = s[0]
             m = m + dm
-            cur = modes(m)
-            report["phase"].append("B")
+            cur = modes(m, "B")
             steps += 1
             w2, r2 = cur
             after = int(np.sum((w2 < 0) & (np.abs(w2) < a)))

@@ -15,10 +15,11 @@ from .build import LIB
 __all__ = ["QStarError", "Lattice", "create_lattice", "load_gauge", "apply_Dw", "apply_Q",
            "lowmodes_at_mass", "pfaffian_sign", "eig_default_opts", "sign_default_opts",
            "set_profiling", "get_profile", "apply_Q_batch", "MLP",
-           "strerror", "QS_F64", "QS_F32", "lib"]
+           "strerror", "QS_F64", "QS_F32", "QS_F16", "QS_BF16", "lib"]
 
-QS_F64, QS_F32 = 0, 1
+QS_F64, QS_F32, QS_F16, QS_BF16 = 0, 1, 2, 3
 QS_LAYOUT_TILED = 16
+Q16_BYTES_PER_SITE = 52     # 16-bit storage: 24 16-bit reals + one FP32 scale per site
 
 
 class QStarError(RuntimeError):
@@ -60,7 +61,7 @@ QS_WINDOW = 24
 class SignOpts(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("m0_max", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("eig", EigOpts), ("step_model", ctypes.c_void_p),
-                ("window_trace", ctypes.POINTER(ctypes.c_double))]
+                ("window_trace", ctypes.POINTER(ctypes.c_double)), ("retreat", ctypes.c_int)]
 
 
 class SignReport(ctypes.Structure):
@@ -89,7 +90,7 @@ class KernelProf(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("dslash", KernelProf * 2)]
+    _fields_ = [("dslash", KernelProf * 4)]
 
 
 def _load():
@@ -122,6 +123,9 @@ def _load():
         "qs_mlp_forward": (I, [P, P, I, P]),
         "qs_mlp_train_step": (I, [P, P, P, I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
         "qs_apply_Q_batch": (I, [ctypes.POINTER(BatchItem), I, I, P]),
+        "qs_convert_spinors": (I, [P, P, I, P, I, I]),
+        "qs_log_det_oo": (I, [P, I, P, P]),
+        "qs_w_eo": (I, [P, D, D, P, P]),
         "qs_apply_Q_norm2_noalloc": (I, [P, D, P, P, I, I, P]),
         "qs_strerror": (ctypes.c_char_p, [I]),
         "qs_last_cuda_error": (ctypes.c_char_p, []),
@@ -176,24 +180,40 @@ def load_gauge(h, su3, theta, csw_su3, csw_u1):
                               float(csw_su3), float(csw_u1)), "load_gauge")
 
 
-def _nrhs(h, t):
+def _nrhs(h, t, prec=None):
     ns = _lib.qs_n_sites(h)
+    if prec in (QS_F16, QS_BF16):
+        nb = t.numel() * t.element_size()
+        n = nb // (ns * Q16_BYTES_PER_SITE)
+        if n * ns * Q16_BYTES_PER_SITE != nb:
+            raise ValueError("16-bit spinor buffer is not a multiple of N_s * 52 bytes")
+        return n
     n = t.numel() // (ns * 24)
     if n * ns * 24 != t.numel():
         raise ValueError("spinor size is not a multiple of N_s * 24 reals")
     return n
 
 
-def apply_Dw(h, m0, inp, out, tiled=False):
-    """qs_apply_Dw on device tensors (float64 or float32; canonical layout, or the
-    site-tiled one with tiled=True)."""
-    _check(_lib.qs_apply_Dw(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
-                            _prec_of(inp) | (QS_LAYOUT_TILED if tiled else 0)), "apply_Dw")
+def _op_prec(t, prec, tiled):
+    p = _prec_of(t) if prec is None else prec
+    if p in (QS_F16, QS_BF16) and not tiled:
+        raise ValueError("16-bit storage exists in the tiled layout only")
+    return p
 
 
-def apply_Q(h, m0, inp, out, tiled=False):
-    _check(_lib.qs_apply_Q(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
-                           _prec_of(inp) | (QS_LAYOUT_TILED if tiled else 0)), "apply_Q")
+def apply_Dw(h, m0, inp, out, tiled=False, prec=None):
+    """qs_apply_Dw on device tensors: float64 or float32 (canonical layout, or the
+    site-tiled one with tiled=True), or prec=QS_F16 / QS_BF16 with byte buffers in
+    the tiled 16-bit format (see include/qstar.h)."""
+    p = _op_prec(inp, prec, tiled)
+    _check(_lib.qs_apply_Dw(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp, p),
+                            p | (QS_LAYOUT_TILED if tiled else 0)), "apply_Dw")
+
+
+def apply_Q(h, m0, inp, out, tiled=False, prec=None):
+    p = _op_prec(inp, prec, tiled)
+    _check(_lib.qs_apply_Q(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp, p),
+                           p | (QS_LAYOUT_TILED if tiled else 0)), "apply_Q")
 
 
 def to_tiled(x, n_sites):
@@ -265,6 +285,26 @@ def pfaffian_sign(h, m0_target, opts=None, step_model=None, trace=False):
     return sg.value, out
 
 
+def log_det_oo(h, masses):
+    """qs_log_det_oo: log|det D^oo(m0)| for each bare mass (numpy array)."""
+    m = np.ascontiguousarray(masses, dtype=np.float64)
+    out = np.zeros(len(m))
+    _check(_lib.qs_log_det_oo(h, len(m), m.ctypes.data, out.ctypes.data), "log_det_oo")
+    return out
+
+
+def w_eo(h, m, mp):
+    """qs_w_eo: (W_eo(m -> m'), log W_eo)."""
+    w, lw = ctypes.c_double(0), ctypes.c_double(0)
+    _check(_lib.qs_w_eo(h, float(m), float(mp), ctypes.byref(w), ctypes.byref(lw)), "w_eo")
+    return w.value, lw.value
+
+
+def convert_spinors(h, inp, in_prec, out, out_prec, nrhs):
+    """qs_convert_spinors: tiled spinors from one precision to another (device buffers)."""
+    _check(_lib.qs_convert_spinors(h, inp.data_ptr(), in_prec, out.data_ptr(), out_prec, nrhs), "convert_spinors")
+
+
 def apply_Q_norm2_noalloc(h, m0, inp, out, norm2):
     """qs_apply_Q_norm2_noalloc: out = Q in and norm2[r] = |out_r|^2 (device tensors),
     with no device allocation by the library."""
@@ -272,26 +312,26 @@ def apply_Q_norm2_noalloc(h, m0, inp, out, norm2):
                                          _prec_of(inp), norm2.data_ptr()), "apply_Q_norm2_noalloc")
 
 
-def apply_Q_batch(entries, tiled=False, stream=None):
+def apply_Q_batch(entries, tiled=False, stream=None, prec=None):
     """qs_apply_Q_batch: one launch over [(lattice, in, out, masses), ...]; masses has one
-    bare mass per right-hand side of that lattice's in/out tensors."""
+    bare mass per right-hand side of that lattice's in/out tensors (prec as for apply_Q)."""
     n = len(entries)
     arr = (BatchItem * n)()
     keep = []
-    prec = None
+    common = None
     for i, (lat, inp, out, masses) in enumerate(entries):
         h = lat.h if hasattr(lat, "h") else lat
         m = (ctypes.c_double * len(masses))(*[float(x) for x in masses])
         keep.append(m)
-        nr = _nrhs(h, inp)
+        p = _op_prec(inp, prec, tiled)
+        nr = _nrhs(h, inp, p)
         if nr != len(masses):
             raise ValueError("one mass per right-hand side")
         arr[i] = BatchItem(h, inp.data_ptr(), out.data_ptr(), nr, m)
-        p = _prec_of(inp)
-        if prec is not None and p != prec:
+        if common is not None and p != common:
             raise TypeError("all items of a batch share one precision")
-        prec = p
-    _check(_lib.qs_apply_Q_batch(arr, n, prec | (QS_LAYOUT_TILED if tiled else 0), _stream_ptr(stream)),
+        common = p
+    _check(_lib.qs_apply_Q_batch(arr, n, common | (QS_LAYOUT_TILED if tiled else 0), _stream_ptr(stream)),
            "apply_Q_batch")
 
 
@@ -330,14 +370,26 @@ class MLP:
         _check(_lib.qs_mlp_get_grads(self.h, flat.ctypes.data), "mlp_get_grads")
         return self._split(flat)
 
+    def _rows(self, t, width, name):
+        import torch
+        if t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != width or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 tensor [B][{width}], got "
+                             f"{t.dtype} {tuple(t.shape)}")
+        return t.shape[0]
+
     def forward(self, X):
         """X: float32 device tensor [B][in] -> device tensor [B][out]."""
         import torch
+        self._rows(X, self.shape[0], "X")
         Y = torch.empty((X.shape[0], self.shape[2]), dtype=torch.float32, device=X.device)
         _check(_lib.qs_mlp_forward(self.h, X.data_ptr(), X.shape[0], Y.data_ptr()), "mlp_forward")
         return Y
 
     def train_step(self, X, T, lr):
+        """One Adam step on X [B][in], T [B][out] (float32 device tensors)."""
+        b = self._rows(X, self.shape[0], "X")
+        if self._rows(T, self.shape[2], "T") != b:
+            raise ValueError("X and T must have the same number of rows")
         loss = ctypes.c_float(0)
         _check(_lib.qs_mlp_train_step(self.h, X.data_ptr(), T.data_ptr(), X.shape[0], float(lr),
                                       ctypes.byref(loss)), "mlp_train_step")
@@ -365,11 +417,12 @@ def set_profiling(h, on):
 
 
 def get_profile(h):
-    """{"f64": {...}, "f32": {...}} with launches, ms, bytes of the operator kernels."""
+    """{"f64": {...}, "f32": {...}, "f16": {...}, "bf16": {...}} with launches, ms and
+    algorithmic bytes of the operator kernels, by spinor precision."""
     p = Profile()
     _check(_lib.qs_get_profile(h, ctypes.byref(p)), "get_profile")
     out = {}
-    for name, i in (("f64", QS_F64), ("f32", QS_F32)):
+    for name, i in (("f64", QS_F64), ("f32", QS_F32), ("f16", QS_F16), ("bf16", QS_BF16)):
         k = p.dslash[i]
         out[name] = {"launches": k.launches, "ms": k.ms, "bytes": k.bytes}
     return out
@@ -386,11 +439,11 @@ class Lattice:
     def load_gauge(self, su3, theta, csw_su3, csw_u1):
         load_gauge(self.h, su3, theta, csw_su3, csw_u1)
 
-    def apply_Dw(self, m0, inp, out, tiled=False):
-        apply_Dw(self.h, m0, inp, out, tiled)
+    def apply_Dw(self, m0, inp, out, tiled=False, prec=None):
+        apply_Dw(self.h, m0, inp, out, tiled, prec)
 
-    def apply_Q(self, m0, inp, out, tiled=False):
-        apply_Q(self.h, m0, inp, out, tiled)
+    def apply_Q(self, m0, inp, out, tiled=False, prec=None):
+        apply_Q(self.h, m0, inp, out, tiled, prec)
 
     def lowmodes_at_mass(self, m0, opts=None, evecs=None, allow_noconv=False):
         return lowmodes_at_mass(self.h, m0, opts, evecs, allow_noconv)

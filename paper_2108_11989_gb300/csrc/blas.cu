@@ -210,6 +210,14 @@ __global__ void d2f_kernel(const double *__restrict__ x, float *__restrict__ y, 
         b[i] = (float)(a[i] * s);
 }
 
+__global__ void f2d_kernel(const float *__restrict__ x, double *__restrict__ y, int64_t nr)
+{
+    const float *a = x + (int64_t)blockIdx.y * nr;
+    double *b = y + (int64_t)blockIdx.y * nr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
 __global__ void axpy_f2d_kernel(double *__restrict__ x, const float *__restrict__ e, const double *coef, int64_t nr)
 {
     double c = coef[blockIdx.y];
@@ -428,6 +436,14 @@ cudaError_t qs_d2f(const double *x, float *y, const double *scale, int k, int64_
 {
     dim3 g(grid_for(nr) / k + 1, k);
     d2f_kernel<<<g, 256, 0, st>>>(x, y, scale, nr);
+    qs_note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t qs_f2d(const float *x, double *y, int k, int64_t nr, cudaStream_t st)
+{
+    dim3 g(grid_for(nr) / k + 1, k);
+    f2d_kernel<<<g, 256, 0, st>>>(x, y, nr);
     qs_note_launches(1);
     return cudaGetLastError();
 }

@@ -24,6 +24,8 @@ cudaError_t qs_rotate(const double *W, int ka, const double2 *C, int kc, int64_t
                       cudaStream_t st, int lowp = 0);
 // y_r = (float)(x_r * scale[r])  (scale on device, may be NULL for 1)
 cudaError_t qs_d2f(const double *x, float *y, const double *scale, int k, int64_t nr, cudaStream_t st);
+// y_r = (double) x_r
+cudaError_t qs_f2d(const float *x, double *y, int k, int64_t nr, cudaStream_t st);
 // x_r += coef[r] * (double) e_r  (coef on device)
 cudaError_t qs_axpy_f2d(double *x, const float *e, const double *coef, int k, int64_t nr, cudaStream_t st);
 // ynew = s1 * (ay - c * y) - s2 * x   (all vectors of the block)

@@ -5,6 +5,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 // Events around operator launches while profiling is on; resolved in batches.
@@ -152,12 +155,8 @@ extern "C" int qs_destroy_lattice(qs_lattice *lat)
 
 extern "C" int64_t qs_n_sites(const qs_lattice *lat) { return lat ? lat->g.Ns : 0; }
 
-template <typename R>
-static DslashArgs<R> make_args(qs_lattice *lat, const double *m0, const void *in, void *out, int nrhs,
-                               int gamma5);
-template <>
-DslashArgs<double> make_args<double>(qs_lattice *lat, const double *m0, const void *in, void *out,
-                                     int nrhs, int gamma5)
+static DslashArgs<double> make_args64(qs_lattice *lat, const double *m0, const void *in, void *out, int nrhs,
+                                      int gamma5)
 {
     DslashArgs<double> d;
     d.g = lat->g; d.links = lat->links64; d.clov = lat->clov64;
@@ -165,77 +164,244 @@ DslashArgs<double> make_args<double>(qs_lattice *lat, const double *m0, const vo
     for (int r = 0; r < nrhs; ++r) d.m0[r] = m0[r];
     return d;
 }
-template <>
-DslashArgs<float> make_args<float>(qs_lattice *lat, const double *m0, const void *in, void *out,
-                                   int nrhs, int gamma5)
+
+// ---- launch-variant autotuner -------------------------------------------------
+// Each operator form (kernel, storage, epilogue, nrhs) on each lattice shape is timed
+// once over all its launch variants (tile shape: right-hand sides per thread and per
+// warp, registers per thread) with CUDA events on the handle's stream; the fastest is
+// kept in the handle and in a process-wide table.  If QS_TUNE_CACHE names a file, the
+// table is read from it at the first use and every new choice is appended to it, so
+// later processes on the same GPU model skip the timing.
+namespace {
+struct TuneCache {
+    std::map<std::string, int> m;
+    bool loaded = false;
+    std::string path;
+};
+TuneCache &tune_cache()
 {
-    DslashArgs<float> d;
-    d.g = lat->g; d.links = lat->links32; d.clov = lat->clov32;
-    d.in = (const float *)in; d.out = (float *)out; d.gamma5 = gamma5; d.nrhs = nrhs;
-    for (int r = 0; r < nrhs; ++r) d.m0[r] = m0[r];
-    return d;
+    static TuneCache c;
+    return c;
+}
+std::mutex g_tune_mu;
+
+std::string tune_key(const qs_lattice *lat, const char *kernel, int storage, int cheb, int nrhs)
+{
+    cudaDeviceProp p;
+    char buf[512];
+    const char *gpu = cudaGetDeviceProperties(&p, lat->device) == cudaSuccess ? p.name : "gpu";
+    snprintf(buf, sizeof(buf), "%s|%s|%d|%d|%d|%dx%d", gpu, kernel, storage, cheb, nrhs, lat->g.L, lat->g.T);
+    for (char *c = buf; *c; ++c)
+        if (*c == ' ') *c = '_';
+    return buf;
 }
 
-template <typename R>
-static int run_typed(qs_lattice *lat, int pi, const double *m0, const void *in, void *out, int nrhs,
-                     int gamma5, int soa)
+int tune_lookup(const std::string &key)
 {
-    DslashArgs<R> d = make_args<R>(lat, m0, in, out, nrhs, gamma5);
-    int &tv = lat->tuned[soa ? 1 : 0][pi][nrhs];
-    if (tv == 0) {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        QS_CUDA(cudaStreamIsCapturing(lat->stream, &cs));
-        if (cs != cudaStreamCaptureStatusNone) {
-            tv = 1 + (qs_dslash_nvariants<R>() > 2 ? 2 : 0);   // cannot time inside a capture
-        } else {
-            cudaEvent_t e0, e1;
-            QS_CUDA(cudaEventCreate(&e0));
-            QS_CUDA(cudaEventCreate(&e1));
-            float best = 1e30f;
-            int bv = 0;
-            for (int v = 0; v < qs_dslash_nvariants<R>(); ++v) {
-                QS_CUDA(qs_dslash_launch<R>(d, nrhs, v, soa, lat->stream));   // warm-up
-                QS_CUDA(cudaEventRecord(e0, lat->stream));
-                for (int rep = 0; rep < 3; ++rep) QS_CUDA(qs_dslash_launch<R>(d, nrhs, v, soa, lat->stream));
-                QS_CUDA(cudaEventRecord(e1, lat->stream));
-                QS_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                QS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) { best = ms; bv = v; }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneCache &c = tune_cache();
+    if (!c.loaded) {
+        c.loaded = true;
+        const char *e = getenv("QS_TUNE_CACHE");
+        if (e && *e) {
+            c.path = e;
+            FILE *f = fopen(e, "r");
+            if (f) {
+                char k[512];
+                int v;
+                while (fscanf(f, "%511s %d", k, &v) == 2) c.m[k] = v;
+                fclose(f);
             }
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            tv = bv + 1;
         }
     }
-    ProfState *pf = (lat->prof && lat->prof->on) ? lat->prof : nullptr;
-    cudaEvent_t ea = nullptr, eb = nullptr;
-    if (pf) {
-        if (pf->pending.size() >= 4096) QS_TRY(prof_resolve(lat));
-        ea = prof_event(pf);
-        eb = prof_event(pf);
-        QS_CUDA(cudaEventRecord(ea, lat->stream));
+    auto it = c.m.find(key);
+    return it == c.m.end() ? -1 : it->second;
+}
+
+void tune_store(const std::string &key, int v)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneCache &c = tune_cache();
+    c.m[key] = v;
+    if (!c.path.empty()) {
+        FILE *f = fopen(c.path.c_str(), "a");
+        if (f) {
+            fprintf(f, "%s %d\n", key.c_str(), v);
+            fclose(f);
+        }
     }
-    cudaError_t e = qs_dslash_launch<R>(d, nrhs, tv - 1, soa, lat->stream);
+}
+
+// time `nv` variants of `launch(v)` on the stream; returns the fastest (0-based)
+template <typename F>
+int time_variants(qs_lattice *lat, int nv, F launch, int *status)
+{
+    *status = QS_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        *status = QS_ECUDA;
+        return 0;
+    }
+    float best = 1e30f;
+    int bv = 0;
+    for (int v = 0; v < nv && *status == QS_OK; ++v) {
+        cudaError_t e = launch(v);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, lat->stream);
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = launch(v);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, lat->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            qs_record_cuda_error(e, "autotune");
+            *status = QS_ECUDA;
+        } else if (ms < best) {
+            best = ms;
+            bv = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return bv;
+}
+
+bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+}  // namespace
+
+// ---- profiling records -----------------------------------------------------------
+static int prof_begin(qs_lattice *lat, cudaEvent_t *ea, cudaEvent_t *eb)
+{
+    ProfState *pf = (lat->prof && lat->prof->on && !capturing(lat->stream)) ? lat->prof : nullptr;
+    *ea = *eb = nullptr;
+    if (!pf) return QS_OK;
+    if (pf->pending.size() >= 4096) QS_TRY(prof_resolve(lat));
+    *ea = prof_event(pf);
+    *eb = prof_event(pf);
+    QS_CUDA(cudaEventRecord(*ea, lat->stream));
+    return QS_OK;
+}
+
+static int prof_end(qs_lattice *lat, cudaEvent_t ea, cudaEvent_t eb, int prec, double bytes)
+{
+    if (!ea) return QS_OK;
+    QS_CUDA(cudaEventRecord(eb, lat->stream));
+    lat->prof->pending.push_back({ea, eb, prec, bytes});
+    return QS_OK;
+}
+
+static int run64(qs_lattice *lat, const double *m0, const void *in, void *out, int nrhs, int gamma5, int soa)
+{
+    DslashArgs<double> d = make_args64(lat, m0, in, out, nrhs, gamma5);
+    int &tv = lat->tuned64[soa ? 1 : 0][nrhs];
+    if (tv == 0) {
+        const std::string key = tune_key(lat, "dslash64", soa, 0, nrhs);
+        int v = tune_lookup(key);
+        if (v < 0 || v >= qs_dslash_nvariants<double>()) {
+            if (capturing(lat->stream)) {
+                v = 2;   // no timing inside a capture: a fixed variant
+            } else {
+                int st = QS_OK;
+                v = time_variants(lat, qs_dslash_nvariants<double>(),
+                                  [&](int q) { return qs_dslash_launch<double>(d, nrhs, q, soa, lat->stream); }, &st);
+                if (st != QS_OK) return st;
+                tune_store(key, v);
+            }
+        }
+        tv = v + 1;
+    }
+    cudaEvent_t ea, eb;
+    QS_TRY(prof_begin(lat, &ea, &eb));
+    cudaError_t e = qs_dslash_launch<double>(d, nrhs, tv - 1, soa, lat->stream);
     qs_note_launches(1);
-    if (pf) {
-        QS_CUDA(cudaEventRecord(eb, lat->stream));
-        pf->pending.push_back({ea, eb, pi == 0 ? QS_F64 : QS_F32,
-                               (double)lat->g.Ns * (48.0 * nrhs + 72.0) * sizeof(R)});
-    }
     if (e != cudaSuccess) {
         qs_record_cuda_error(e, "dslash launch");
         return QS_ECUDA;
     }
-    return QS_OK;
+    return prof_end(lat, ea, eb, QS_F64, (double)lat->g.Ns * (48.0 * nrhs + 72.0) * 8);
+}
+
+static int prec_of_storage(int storage)
+{
+    return storage == QS_D32_F16 ? QS_F16 : storage == QS_D32_BF16 ? QS_BF16 : QS_F32;
+}
+
+int qs_d32_run(qs_lattice *lat, int storage, const double *m0, const void *in, void *out, int nrhs, int gamma5,
+               const void *cheb_y, const void *cheb_x, double cheb_c, double cheb_s1, double cheb_s2)
+{
+    D32Call c;
+    c.g = lat->g;
+    c.links = lat->links32;
+    c.clov = lat->clov32;
+    c.in = in;
+    c.out = out;
+    c.y = cheb_y;
+    c.x = cheb_x;
+    c.storage = storage;
+    c.nrhs = nrhs;
+    c.gamma5 = gamma5;
+    c.cheb = cheb_y != nullptr;
+    c.cheb_c = cheb_c;
+    c.cheb_s1 = cheb_s1;
+    c.cheb_s2 = cheb_s2;
+    c.m0 = m0;
+    int &tv = lat->tuned32[storage][c.cheb][nrhs];
+    if (tv == 0) {
+        const std::string key = tune_key(lat, "dslash32", storage, c.cheb, nrhs);
+        int v = tune_lookup(key);
+        if (v < 0 || v >= qs_d32_nvariants()) {
+            if (capturing(lat->stream)) {
+                v = 1;   // no timing inside a capture: a fixed variant
+            } else {
+                // timing writes `out` only (in, y and x are read): harmless to the caller
+                int st = QS_OK;
+                v = time_variants(lat, qs_d32_nvariants(), [&](int q) { return qs_d32_launch(c, q, lat->stream); }, &st);
+                if (st != QS_OK) return st;
+                tune_store(key, v);
+            }
+        }
+        tv = v + 1;
+    }
+    cudaEvent_t ea, eb;
+    QS_TRY(prof_begin(lat, &ea, &eb));
+    cudaError_t e = qs_d32_launch(c, tv - 1, lat->stream);
+    qs_note_launches(1);
+    if (e != cudaSuccess) {
+        qs_record_cuda_error(e, "dslash32 launch");
+        return QS_ECUDA;
+    }
+    // algorithmic bytes: per doubled site, each right-hand side's spinor in and out
+    // (plus y and x for the Chebyshev epilogue), and once per launch 36 link + 36 SW
+    // FP32 reals (each physical link and SW block serves the site and its mirror)
+    const double vs = (double)qs_d32_vec_bytes(storage, 1);
+    const double bytes = (double)lat->g.Ns * (vs * (c.cheb ? 4 : 2) * nrhs + 72.0 * 4);
+    return prof_end(lat, ea, eb, prec_of_storage(storage), bytes);
 }
 
 int qs_dslash_run(qs_lattice *lat, int prec, const double *m0, const void *in, void *out, int nrhs,
                   int gamma5, int soa)
 {
-    if (prec == QS_F64) return run_typed<double>(lat, 0, m0, in, out, nrhs, gamma5, soa);
-    if (prec == QS_F32) return run_typed<float>(lat, 1, m0, in, out, nrhs, gamma5, soa);
+    if (prec == QS_F64) return run64(lat, m0, in, out, nrhs, gamma5, soa);
+    if (prec == QS_F32) return qs_d32_run(lat, soa ? QS_D32_F32_TILED : QS_D32_F32_CANON, m0, in, out, nrhs, gamma5);
+    if (prec == QS_F16 && soa) return qs_d32_run(lat, QS_D32_F16, m0, in, out, nrhs, gamma5);
+    if (prec == QS_BF16 && soa) return qs_d32_run(lat, QS_D32_BF16, m0, in, out, nrhs, gamma5);
     return QS_EINVAL;
+}
+
+// bytes of one right-hand side of the given precision and layout (0: not supported)
+static size_t vec_bytes(const qs_lattice *lat, int prec, int tiled)
+{
+    switch (prec) {
+    case QS_F64: return (size_t)lat->g.Ns * 24 * 8;
+    case QS_F32: return (size_t)lat->g.Ns * 24 * 4;
+    case QS_F16:
+    case QS_BF16: return tiled ? (size_t)qs_d32_vec_bytes(QS_D32_F16, lat->g.Ns) : 0;
+    default: return 0;
+    }
 }
 
 int qs_apply_op(qs_lattice *lat, const double *m0, const void *in, void *out, int nrhs, int prec,
@@ -245,13 +411,40 @@ int qs_apply_op(qs_lattice *lat, const double *m0, const void *in, void *out, in
     if (!lat->gauge_loaded) return QS_EINVAL;
     const int tiled = (prec & QS_LAYOUT_TILED) ? 1 : 0;
     prec &= ~QS_LAYOUT_TILED;
-    if (prec != QS_F64 && prec != QS_F32) return QS_EINVAL;
-    size_t bytes = (size_t)nrhs * lat->g.Ns * 24 * (prec == QS_F64 ? 8 : 4);
+    const size_t vb = vec_bytes(lat, prec, tiled);
+    if (!vb) return QS_EINVAL;
+    size_t bytes = (size_t)nrhs * vb;
     const char *a = (const char *)in, *b = (const char *)out;
     if (a < b + bytes && b < a + bytes) return QS_EINVAL;      // overlap
     if (((uintptr_t)in | (uintptr_t)out) & 15) return QS_EINVAL; // vector loads need 16 B
     QS_CUDA(cudaSetDevice(lat->device));
     return qs_dslash_run(lat, prec, m0, in, out, nrhs, gamma5, tiled);
+}
+
+static int storage_of_prec(int prec)
+{
+    switch (prec) {
+    case QS_F64: return QS_D32_F64_TILED;
+    case QS_F32: return QS_D32_F32_TILED;
+    case QS_F16: return QS_D32_F16;
+    case QS_BF16: return QS_D32_BF16;
+    default: return -1;
+    }
+}
+
+extern "C" int qs_convert_spinors(qs_lattice *lat, const void *in, int in_prec, void *out, int out_prec, int nrhs)
+{
+    if (!lat || !in || !out || nrhs < 1) return QS_EINVAL;
+    const int a = storage_of_prec(in_prec & ~QS_LAYOUT_TILED), b = storage_of_prec(out_prec & ~QS_LAYOUT_TILED);
+    if (a < 0 || b < 0 || a == b) return QS_EINVAL;
+    const size_t na = (size_t)nrhs * vec_bytes(lat, in_prec & ~QS_LAYOUT_TILED, 1);
+    const size_t nb = (size_t)nrhs * vec_bytes(lat, out_prec & ~QS_LAYOUT_TILED, 1);
+    const char *x = (const char *)in, *y = (const char *)out;
+    if (x < y + nb && y < x + na) return QS_EINVAL;
+    if (((uintptr_t)in | (uintptr_t)out) & 15) return QS_EINVAL;
+    QS_CUDA(cudaSetDevice(lat->device));
+    QS_CUDA(qs_convert_tiled(a, b, in, out, lat->g.Ns, nrhs, lat->stream));
+    return QS_OK;
 }
 
 extern "C" int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec)
@@ -287,27 +480,21 @@ extern "C" const char *qs_strerror(int status)
 
 extern "C" const char *qs_last_cuda_error(void) { return g_last_cuda_error; }
 
-template <typename R>
-static int batch_typed(const qs_batch_item *items, int n, int tiled, cudaStream_t st)
+static int batch64(const qs_batch_item *items, int n, int tiled, cudaStream_t st)
 {
-    BatchArgs<R> a;
+    BatchArgs<double> a;
     memset(&a, 0, sizeof(a));
     a.n = n;
     a.gamma5 = 1;
     unsigned off = 0;
     for (int i = 0; i < n; ++i) {
         qs_lattice *lat = items[i].lat;
-        BatchItem<R> &it = a.item[i];
+        BatchItem<double> &it = a.item[i];
         it.g = lat->g;
-        if (sizeof(R) == 8) {
-            it.links = (const typename LinkT<R>::T *)lat->links64;
-            it.clov = (const R *)lat->clov64;
-        } else {
-            it.links = (const typename LinkT<R>::T *)lat->links32;
-            it.clov = (const R *)lat->clov32;
-        }
-        it.in = (const R *)items[i].in;
-        it.out = (R *)items[i].out;
+        it.links = lat->links64;
+        it.clov = lat->clov64;
+        it.in = (const double *)items[i].in;
+        it.out = (double *)items[i].out;
         it.nrhs = items[i].nrhs;
         for (int r = 0; r < it.nrhs; ++r) it.m0[r] = items[i].m0[r];
         a.off[i] = off;
@@ -316,9 +503,30 @@ static int batch_typed(const qs_batch_item *items, int n, int tiled, cudaStream_
         off += (unsigned)nb;
     }
     a.off[n] = off;
-    cudaError_t e = qs_dslash_batch_launch<R>(a, tiled, st);
+    cudaError_t e = qs_dslash_batch_launch<double>(a, tiled, st);
     if (e != cudaSuccess) {
         qs_record_cuda_error(e, "batched dslash launch");
+        return QS_ECUDA;
+    }
+    return QS_OK;
+}
+
+static int batch32(const qs_batch_item *items, int n, int storage, cudaStream_t st)
+{
+    D32BatchItem b[QS_BATCH_MAX];
+    for (int i = 0; i < n; ++i) {
+        qs_lattice *lat = items[i].lat;
+        b[i].g = lat->g;
+        b[i].links = lat->links32;
+        b[i].clov = lat->clov32;
+        b[i].in = items[i].in;
+        b[i].out = items[i].out;
+        b[i].nrhs = items[i].nrhs;
+        for (int r = 0; r < items[i].nrhs; ++r) b[i].m0[r] = items[i].m0[r];
+    }
+    cudaError_t e = qs_d32_batch_launch(b, n, storage, 1, st);
+    if (e != cudaSuccess) {
+        qs_record_cuda_error(e, "batched dslash32 launch");
         return QS_ECUDA;
     }
     return QS_OK;
@@ -329,8 +537,6 @@ extern "C" int qs_apply_Q_batch(const qs_batch_item *items, int n, int prec, voi
     if (!items || n < 1 || n > QS_BATCH_MAX) return QS_EINVAL;
     const int tiled = (prec & QS_LAYOUT_TILED) ? 1 : 0;
     prec &= ~QS_LAYOUT_TILED;
-    if (prec != QS_F64 && prec != QS_F32) return QS_EINVAL;
-    const size_t rs = prec == QS_F64 ? 8 : 4;
     int dev = -1;
     for (int i = 0; i < n; ++i) {
         const qs_batch_item &it = items[i];
@@ -338,13 +544,16 @@ extern "C" int qs_apply_Q_batch(const qs_batch_item *items, int n, int prec, voi
         if (!it.lat->gauge_loaded) return QS_EINVAL;
         if (dev >= 0 && it.lat->device != dev) return QS_EINVAL;
         dev = it.lat->device;
-        size_t bytes = (size_t)it.nrhs * it.lat->g.Ns * 24 * rs;
+        const size_t vb = vec_bytes(it.lat, prec, tiled);
+        if (!vb) return QS_EINVAL;
+        size_t bytes = (size_t)it.nrhs * vb;
         const char *a = (const char *)it.in, *b = (const char *)it.out;
         if (a < b + bytes && b < a + bytes) return QS_EINVAL;
         if (((uintptr_t)it.in | (uintptr_t)it.out) & 15) return QS_EINVAL;
     }
     QS_CUDA(cudaSetDevice(dev));
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == QS_F64) return batch_typed<double>(items, n, tiled, st);
-    return batch_typed<float>(items, n, tiled, st);
+    if (prec == QS_F64) return batch64(items, n, tiled, st);
+    if (prec == QS_F32) return batch32(items, n, tiled ? QS_D32_F32_TILED : QS_D32_F32_CANON, st);
+    return batch32(items, n, prec == QS_F16 ? QS_D32_F16 : QS_D32_BF16, st);
 }

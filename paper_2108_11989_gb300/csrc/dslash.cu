@@ -1,5 +1,6 @@
 // The O(a)-improved Wilson-Dirac operator D and Q = gamma_5 D on the C*-doubled
-// lattice (Sec. 2 operator, Sec. 3 doublet and Q).  One thread per doubled site;
+// lattice (Sec. 2 operator, Sec. 3 doublet and Q) in FP64 arithmetic (the FP32-arithmetic
+// form for FP32 and 16-bit storage is dslash32.cu).  One thread per doubled site;
 // each thread forms
 //   out = (4 + m0) psi + A psi - 1/2 sum_mu [ V (1 - g_mu) psi(x+mu) + V^+ (1 + g_mu) psi(x-mu) ]
 // and, for Q, flips the sign of spins 2, 3.  (1 -+ g_mu) has rank 2: in the
@@ -9,6 +10,7 @@
 // and only the half spinor h is multiplied by the link.
 #include "qs_internal.cuh"
 #include "dslash.cuh"
+#include "stencil.cuh"
 
 namespace {
 
@@ -195,67 +197,6 @@ __device__ __forceinline__ void mul_link_dag(const C2<R> U[9], bool cj, const C2
         }
 }
 
-// Coordinates of a doubled site: x in [0, 2L), y, z in [0, L), t in [0, T);
-// row = (t L + z) L + y; p = row L + (x mod L) is the physical site.
-struct Site {
-    int s, x, y, z, t, row, p;
-};
-
-__device__ __forceinline__ Site site_of(const Geom &g, int s)
-{
-    Site c;
-    c.s = s;
-    c.row = s / g.L2;
-    c.x = s - c.row * g.L2;
-    int r = c.row;
-    c.y = r % g.L;
-    r /= g.L;
-    c.z = r % g.L;
-    c.t = r / g.L;
-    c.p = c.row * g.L + (c.x >= g.L ? c.x - g.L : c.x);
-    return c;
-}
-
-struct Nb {
-    int s, p;
-    bool mir;
-};
-
-// neighbour x + STEP mu (same rules as qs_nbr: x periodic over 2L; crossing y or z
-// with C* there also moves x by L; t periodic or antiperiodic)
-template <int MU, int STEP>
-__device__ __forceinline__ Nb nbr_of(const Geom &g, const Site &c, int *sg)
-{
-    int x = c.x, row = c.row;
-    *sg = 1;
-    const int L = g.L, L2 = g.L2;
-    if (MU == 0) {
-        const int LL = L * L;
-        if (STEP > 0) row = (c.t == g.T - 1) ? row - (g.T - 1) * LL : row + LL;
-        else row = (c.t == 0) ? row + (g.T - 1) * LL : row - LL;
-        if (g.t_anti && ((STEP > 0 && c.t == g.T - 1) || (STEP < 0 && c.t == 0))) *sg = -1;
-    } else if (MU == 1) {
-        if (STEP > 0) x = (x == L2 - 1) ? 0 : x + 1;
-        else x = (x == 0) ? L2 - 1 : x - 1;
-    } else {
-        const int coord = MU == 2 ? c.y : c.z;
-        const int stride = MU == 2 ? 1 : L;
-        const int cst = MU == 2 ? g.cstar_y : g.cstar_z;
-        bool wrap = STEP > 0 ? (coord == L - 1) : (coord == 0);
-        if (wrap) {
-            row += STEP > 0 ? -(L - 1) * stride : (L - 1) * stride;
-            if (cst) x = x >= L ? x - L : x + L;
-        } else {
-            row += STEP * stride;
-        }
-    }
-    Nb n;
-    n.s = row * L2 + x;
-    n.mir = x >= L;
-    n.p = row * L + (n.mir ? x - L : x);
-    return n;
-}
-
 template <int MU, bool SOA, typename R>
 __device__ __forceinline__ void hop_dir(const Geom &g, const typename LinkT<R>::T *__restrict__ links,
                                         const R *__restrict__ in, const Site &c, bool mir, C2<R> acc[12])
@@ -299,12 +240,6 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const typename LinkT<R>::
     }
 }
 
-// One thread per (doubled site, right-hand side).  A block handles 128 consecutive
-// sites of one right-hand side; the right-hand side runs fastest over consecutive
-// blocks, so the blocks of one site tile run together and share the link and
-// SW-term loads through L1/L2.  Site coordinates are computed once per thread in
-// 32-bit arithmetic; every neighbour and physical index follows by adds and
-// compares (no division in the stencil).
 // D (or Q) at doubled site s for right-hand side r: the whole stencil of one site.
 template <typename R, bool SOA>
 __device__ __forceinline__ void dslash_site(const Geom &g, const typename LinkT<R>::T *__restrict__ links,
@@ -420,24 +355,10 @@ static cudaError_t launch_variant(const DslashArgs<R> &a, int soa, cudaStream_t 
 }
 
 // Launch-bound variants (minimum resident 128-thread blocks per SM); the
-// autotuner in capi.cu picks one per (layout, precision, nrhs) by timing.
-template <>
-int qs_dslash_nvariants<float>() { return 5; }
+// autotuner in capi.cu picks one per (layout, nrhs) by timing.  This kernel serves
+// the FP64 operator; FP32 arithmetic runs in dslash32.cu.
 template <>
 int qs_dslash_nvariants<double>() { return 4; }
-
-template <>
-cudaError_t qs_dslash_launch<float>(DslashArgs<float> a, int nrhs, int variant, int soa, cudaStream_t st)
-{
-    a.nrhs = nrhs;
-    switch (variant) {
-    case 0: return launch_variant<float, 3>(a, soa, st);
-    case 1: return launch_variant<float, 4>(a, soa, st);
-    case 2: return launch_variant<float, 5>(a, soa, st);
-    case 3: return launch_variant<float, 6>(a, soa, st);
-    default: return launch_variant<float, 8>(a, soa, st);
-    }
-}
 
 template <>
 cudaError_t qs_dslash_launch<double>(DslashArgs<double> a, int nrhs, int variant, int soa, cudaStream_t st)
@@ -478,5 +399,4 @@ cudaError_t qs_dslash_batch_launch(const BatchArgs<R> &a, int soa, cudaStream_t 
     qs_note_launches(1);
     return cudaGetLastError();
 }
-template cudaError_t qs_dslash_batch_launch<float>(const BatchArgs<float> &, int, cudaStream_t);
 template cudaError_t qs_dslash_batch_launch<double>(const BatchArgs<double> &, int, cudaStream_t);

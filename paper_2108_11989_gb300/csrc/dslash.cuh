@@ -50,10 +50,41 @@ cudaError_t qs_dslash_launch(DslashArgs<R> a, int nrhs, int variant, int soa, cu
 template <typename R>
 int qs_dslash_nvariants();
 
-// Picks (and caches in the handle) the fastest variant for this precision and
-// nrhs by timing each once on the handle's stream, then launches it.
-int qs_dslash_run(qs_lattice *lat, int prec, const double *m0, const void *in, void *out,
-                  int nrhs, int gamma5, int soa = 0);
+
+// ---- FP32-arithmetic operator (dslash32.cu) for FP32 and 16-bit storage ------
+enum { QS_D32_F32_TILED = 0, QS_D32_F32_CANON = 1, QS_D32_F16 = 2, QS_D32_BF16 = 3,
+       QS_D32_F64_TILED = 4 /* conversions only */ };
+
+struct D32Call {
+    Geom g;
+    const float2 *links;   // [mu][9][Vphys] FP32
+    const float2 *clov;    // [2][18][Vphys] FP32 pairs (packed SW blocks)
+    const void *in;        // nrhs vectors, vector r at in + r * qs_d32_vec_bytes(storage, Ns)
+    void *out;
+    const void *y, *x;     // cheb = 1: out = s1 (Q in - c y) - s2 x
+    int storage, nrhs, gamma5, cheb;
+    double cheb_c, cheb_s1, cheb_s2;
+    const double *m0;      // host, nrhs masses
+};
+int qs_d32_nvariants();
+int64_t qs_d32_vec_bytes(int storage, int64_t Ns);
+cudaError_t qs_d32_launch(const D32Call &c, int variant, cudaStream_t st);
+// k vectors from one tiled storage to another (QS_D32_F32_TILED, _F16, _BF16, _F64_TILED)
+cudaError_t qs_convert_tiled(int from, int to, const void *in, void *out, int64_t Ns, int k, cudaStream_t st);
+// FP64 solver-layout block of k vectors <-> 16-bit scaled storage
+cudaError_t qs_q16_from_f64(int storage, const double *in, void *out, int64_t Ns, int k, cudaStream_t st);
+cudaError_t qs_f64_from_q16(int storage, const void *in, double *out, int64_t Ns, int k, cudaStream_t st);
+// Batched persistent form: up to QS_BATCH_MAX lattices of any volume, one launch; the
+// blocks loop over (lattice, right-hand-side group, site tile) work items.
+struct D32BatchItem {
+    Geom g;
+    const float2 *links, *clov;
+    const void *in;
+    void *out;
+    int nrhs;
+    double m0[QS_BATCH_RHS];
+};
+cudaError_t qs_d32_batch_launch(const D32BatchItem *items, int n, int storage, int gamma5, cudaStream_t st);
 
 // one vector from the solver layout to the canonical layout (FP64)
 cudaError_t qs_soa_to_aos(const double *in, double *out, int64_t Ns, cudaStream_t st);

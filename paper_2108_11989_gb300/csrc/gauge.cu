@@ -5,6 +5,7 @@
 // whose mirror half carries the charge-conjugate links U^*, theta -> -theta.
 #include "qs_internal.cuh"
 
+#include <math.h>
 #include <stdio.h>
 
 namespace {
@@ -106,7 +107,7 @@ __device__ M3 field_strength(const Geom &g, const double2 *su3, const double *th
 //   A_+- = (i/2) [[B3, B1 - i B2], [B1 + i B2, -B3]],
 //   B1 = +-F01 - F23, B2 = +-F02 + F13, B3 = +-F03 - F12   (0 = t, 1 = x, 2 = y, 3 = z).
 __global__ void clover_build_kernel(Geom g, const double2 *su3, const double *th, double csu3,
-                                    double cu1, double *clov, float *clov32)
+                                    double cu1, double *clov, float2 *clov32)
 {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= g.Vphys) return;
@@ -133,18 +134,18 @@ __global__ void clover_build_kernel(Geom g, const double2 *su3, const double *th
                 A[a + 3][b] = 0.5 * mul_i(B1[k] + mul_i(B2[k]));
             }
         double *dst = clov + (int64_t)blk * 36 * g.Vphys;
-        float *d32 = clov32 + (int64_t)blk * 36 * g.Vphys;
-        for (int i = 0; i < 6; ++i) {
-            dst[i * g.Vphys + p] = A[i][i].re;
-            d32[i * g.Vphys + p] = (float)A[i][i].re;
-        }
+        // FP32 copy as pairs [2][18][Vphys]: (A_00, A_11), (A_22, A_33), (A_44, A_55),
+        // then the strict-lower entries (re, im) in row order
+        float2 *d32 = clov32 + (int64_t)blk * 18 * g.Vphys;
+        for (int i = 0; i < 6; ++i) dst[i * g.Vphys + p] = A[i][i].re;
+        for (int q = 0; q < 3; ++q)
+            d32[q * g.Vphys + p] = make_float2((float)A[2 * q][2 * q].re, (float)A[2 * q + 1][2 * q + 1].re);
         for (int i = 1; i < 6; ++i)
             for (int j = 0; j < i; ++j) {
                 int k = 6 + 2 * qs_tri(i, j);
                 dst[k * g.Vphys + p] = A[i][j].re;
                 dst[(k + 1) * g.Vphys + p] = A[i][j].im;
-                d32[k * g.Vphys + p] = (float)A[i][j].re;
-                d32[(k + 1) * g.Vphys + p] = (float)A[i][j].im;
+                d32[(3 + qs_tri(i, j)) * g.Vphys + p] = make_float2((float)A[i][j].re, (float)A[i][j].im);
             }
     }
 }
@@ -169,12 +170,14 @@ __global__ void pack_links_kernel(Geom g, const double2 *su3, const double *th, 
 
 // max over physical sites and both chiral blocks of the Frobenius norm of the SW
 // term block (an upper bound of its spectral norm); the mirror block S conj(A) S
-// has the same norm.  Positive doubles order like their bit patterns.
-__global__ void clover_norm_kernel(Geom g, const double *clov, unsigned long long *out)
+// has the same norm.  A non-finite SW entry or link anywhere makes the result +inf.
+// Positive doubles (and +inf) order like their bit patterns.
+__global__ void clover_norm_kernel(Geom g, const double *clov, const double2 *links, unsigned long long *out)
 {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double m = 0;
     if (p < g.Vphys) {
+        bool finite = true;
         for (int b = 0; b < 2; ++b) {
             double f = 0;
             for (int i = 0; i < 6; ++i) {
@@ -185,8 +188,14 @@ __global__ void clover_norm_kernel(Geom g, const double *clov, unsigned long lon
                 double d = clov[(int64_t)(b * 36 + k) * g.Vphys + p];
                 f += 2 * d * d;
             }
+            finite = finite && isfinite(f);
             m = fmax(m, sqrt(f));
         }
+        for (int k = 0; k < 36; ++k) {
+            double2 v = links[(int64_t)k * g.Vphys + p];
+            finite = finite && isfinite(v.x) && isfinite(v.y);
+        }
+        if (!finite) m = INFINITY;
     }
     atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
@@ -226,7 +235,7 @@ extern "C" int qs_load_gauge(qs_lattice *lat, const double *su3, const double *u
         if ((e = cudaMalloc(&lat->links64, nl * sizeof(double2))) != cudaSuccess) { fail(e, "malloc links64"); break; }
         if ((e = cudaMalloc(&lat->links32, nl * sizeof(float2))) != cudaSuccess) { fail(e, "malloc links32"); break; }
         if ((e = cudaMalloc(&lat->clov64, (size_t)g.Vphys * 72 * sizeof(double))) != cudaSuccess) { fail(e, "malloc clov64"); break; }
-        if ((e = cudaMalloc(&lat->clov32, (size_t)g.Vphys * 72 * sizeof(float))) != cudaSuccess) { fail(e, "malloc clov32"); break; }
+        if ((e = cudaMalloc(&lat->clov32, (size_t)g.Vphys * 36 * sizeof(float2))) != cudaSuccess) { fail(e, "malloc clov32"); break; }
         if ((e = cudaMemcpyAsync(d_su3, su3, nl * sizeof(double2), cudaMemcpyHostToDevice, lat->stream)) != cudaSuccess) { fail(e, "copy su3"); break; }
         if (u1_theta && (e = cudaMemcpyAsync(d_th, u1_theta, (size_t)g.Vphys * 4 * sizeof(double), cudaMemcpyHostToDevice, lat->stream)) != cudaSuccess) { fail(e, "copy theta"); break; }
         int nb = (int)((g.Vphys + 127) / 128);
@@ -240,7 +249,8 @@ extern "C" int qs_load_gauge(qs_lattice *lat, const double *su3, const double *u
             d_nm = (unsigned long long *)d_th;
         }
         if ((e = cudaMemsetAsync(d_nm, 0, sizeof(unsigned long long), lat->stream)) != cudaSuccess) { fail(e, "memset"); break; }
-        clover_norm_kernel<<<nb, 128, 0, lat->stream>>>(g, lat->clov64, d_nm);
+        clover_norm_kernel<<<nb, 128, 0, lat->stream>>>(g, lat->clov64, lat->links64, d_nm);
+        qs_note_launches(3);
         if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "clover_norm_kernel"); break; }
         unsigned long long hn = 0;
         if ((e = cudaMemcpyAsync(&hn, d_nm, sizeof(hn), cudaMemcpyDeviceToHost, lat->stream)) != cudaSuccess) { fail(e, "copy norm"); break; }
@@ -248,6 +258,7 @@ extern "C" int qs_load_gauge(qs_lattice *lat, const double *su3, const double *u
         double dn;
         memcpy(&dn, &hn, sizeof(dn));
         lat->clov_norm = dn;
+        if (!isfinite(dn)) st = QS_ENUMERIC;   // NaN / Inf in the gauge field
     } while (0);
     cudaFree(d_su3);
     cudaFree(d_th);

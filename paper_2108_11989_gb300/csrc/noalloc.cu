@@ -23,26 +23,38 @@ static double *g_noalloc_ptr[256];
 template <typename R>
 static int run(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, double *norm2, double *scratch)
 {
-    DslashArgs<R> d;
-    d.g = lat->g;
-    d.in = (const R *)in;
-    d.out = (R *)out;
-    d.gamma5 = 1;
-    d.nrhs = nrhs;
-    for (int r = 0; r < nrhs; ++r) d.m0[r] = m0;
-    const int pi = sizeof(R) == 8 ? 0 : 1;
-    if (sizeof(R) == 8) {
-        d.links = (const typename LinkT<R>::T *)lat->links64;
-        d.clov = (const R *)lat->clov64;
-    } else {
-        d.links = (const typename LinkT<R>::T *)lat->links32;
-        d.clov = (const R *)lat->clov32;
-    }
     // the variant the autotuner already chose, else a fixed one (timing the
     // variants would create events)
-    int tv = lat->tuned[0][pi][nrhs];
-    int variant = tv > 0 ? tv - 1 : (qs_dslash_nvariants<R>() > 2 ? 2 : 0);
-    QS_CUDA(qs_dslash_launch<R>(d, nrhs, variant, 0, lat->stream));
+    if (sizeof(R) == 8) {
+        DslashArgs<double> d;
+        d.g = lat->g;
+        d.in = (const double *)in;
+        d.out = (double *)out;
+        d.gamma5 = 1;
+        d.nrhs = nrhs;
+        for (int r = 0; r < nrhs; ++r) d.m0[r] = m0;
+        d.links = lat->links64;
+        d.clov = lat->clov64;
+        const int tv = lat->tuned64[0][nrhs];
+        QS_CUDA(qs_dslash_launch<double>(d, nrhs, tv > 0 ? tv - 1 : 2, 0, lat->stream));
+    } else {
+        double m[QS_MAX_RHS];
+        for (int r = 0; r < nrhs; ++r) m[r] = m0;
+        D32Call c;
+        memset(&c, 0, sizeof(c));
+        c.g = lat->g;
+        c.links = lat->links32;
+        c.clov = lat->clov32;
+        c.in = in;
+        c.out = out;
+        c.storage = QS_D32_F32_CANON;
+        c.nrhs = nrhs;
+        c.gamma5 = 1;
+        c.m0 = m;
+        const int tv = lat->tuned32[QS_D32_F32_CANON][0][nrhs];
+        QS_CUDA(qs_d32_launch(c, tv > 0 ? tv - 1 : 1, lat->stream));
+    }
+    qs_note_launches(1);
     QS_CUDA(qs_norm2<R>((const R *)out, nrhs, lat->g.Ns * 24, scratch, norm2, lat->stream));
     return QS_OK;
 }

@@ -46,12 +46,16 @@ struct qs_lattice {
     // V = U exp(i theta) on the physical lattice, SoA [mu][9][Vphys] complex
     double2 *links64;
     float2 *links32;
-    // SW term A on the physical lattice: [72][Vphys] reals (two packed 6x6
-    // Hermitian blocks); the mirror site's blocks are derived on the fly
+    // SW term A on the physical lattice (two packed 6x6 Hermitian blocks); the mirror
+    // site's blocks are derived on the fly.  FP64: [72][Vphys] reals (per block 6 real
+    // diagonals, then 15 strict-lower (re, im)); FP32: [2][18][Vphys] pairs (per block
+    // 3 pairs of diagonals, then the 15 strict-lower entries)
     double *clov64;
-    float *clov32;
-    // autotuned Dslash launch variant + 1 per [layout][precision][nrhs] (0: not tuned)
-    int tuned[2][2][65];
+    float2 *clov32;
+    // autotuned launch variant + 1 (0: not tuned): FP64 operator per [layout][nrhs],
+    // FP32-arithmetic operator per [storage][Chebyshev epilogue][nrhs]
+    int tuned64[2][65];
+    int tuned32[4][2][65];
     // solver workspace (allocated on first use, see solver.cu)
     struct Workspace *ws;
     // kernel profiling state (capi.cu), NULL when off
@@ -145,3 +149,13 @@ Geom qs_make_geom(int L, int T, int cstar_mask, int t_anti);
 
 // process-wide count of kernel launches made by the library
 void qs_note_launches(int n);
+
+// operator launch with the handle's autotuned variant (capi.cu).  prec: QS_F64, QS_F32,
+// QS_F16, QS_BF16 (the 16-bit ones in the tiled layout only); soa: tiled layout
+int qs_dslash_run(qs_lattice *lat, int prec, const double *m0, const void *in, void *out, int nrhs,
+                  int gamma5, int soa);
+// FP32-arithmetic operator for a storage QS_D32_*, optionally with the Chebyshev
+// epilogue out = s1 (Q in - c y) - s2 x (cheb_y != NULL)
+int qs_d32_run(qs_lattice *lat, int storage, const double *m0, const void *in, void *out, int nrhs, int gamma5,
+               const void *cheb_y = nullptr, const void *cheb_x = nullptr, double cheb_c = 0,
+               double cheb_s1 = 0, double cheb_s2 = 0);

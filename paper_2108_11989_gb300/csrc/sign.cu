@@ -2,12 +2,19 @@
 // eigenvalue it uses comes from the GPU eigensolver with its residual bound r
 // (some eigenvalue of Q lies within r of each Ritz value theta).
 //
+// lambda_bar at a mass is the smallest |theta| of the block and lo = min (|theta_j| - r_j)
+// its certified lower bound, both over the values that carry information (the converged
+// ones, and every other value with r_j <= |theta_j| / 2).
+//
 // Step A follows the enumerated algorithm of Sec. 3: m_{n+1} = m_n + c lambda_bar_n;
-// stop for step B when lambda_bar decreases, stop with the sign once m > m0_max.
-// The no-crossing certificate of eq. derivativebound (|lambda'| <= 1) is checked
-// with lower bounds: (lb_n - r_n) + (lb_{n+1} - r_{n+1}) >= m_{n+1} - m_n; a step
-// that fails it is shortened to m_n + 0.95 (lb_n - r_n), the edge of the interval
-// around m_n that is free of crossings.
+// step 3 (lambda_bar decreases) hands over to step B, step 4 (m > m0_max) ends with the
+// sign found so far.  At finite accuracy the no-crossing certificate of eq.
+// derivativebound (|lambda'| <= 1) is checked with lower bounds,
+// lo_n + lo_{n+1} >= m_{n+1} - m_n; with exact eigenvalues and c < 2 it holds whenever
+// lambda_bar does not decrease.  A step that fails it is treated as step 3: step B starts
+// from m_n, the last mass up to which the flow is certified.  With the `retreat` option
+// an uncertified step is instead shortened to m_n + 0.95 lo_n (the edge of the interval
+// around m_n that is free of crossings), and step B starts there if lambda_bar decreased.
 //
 // Step B (our reading; the paper defers to other work): at mass m with tracked
 // window |theta_0| <= ... (all with residual bounds), pick the widest gap between
@@ -32,6 +39,9 @@ extern "C" void qs_sign_default_opts(qs_sign_opts *o)
     o->c = 1.9;
     o->m0_max = 0.0;
     o->max_steps = 400;
+    o->step_model = nullptr;
+    o->window_trace = nullptr;
+    o->retreat = 0;
     qs_eig_default_opts(&o->eig);
     // certificates carry the residual bound r, so any r < |theta| is rigorous; a
     // moderate relative accuracy keeps every mass point cheap
@@ -62,6 +72,25 @@ double now_s()
     return ts.tv_sec + 1e-9 * ts.tv_nsec;
 }
 
+// lambda_bar (smallest |theta|) and its certified lower bound min (|theta_j| - r_j) over
+// the values of the block that carry information: the nwant converged ones and every
+// other value with r_j <= |theta_j| / 2 (larger residuals belong to unconverged mixtures).
+// The solver orders the block by theta^2 + r^2, so the smallest lower bound need not
+// belong to theta[0].
+void lambda_bar(const Ritz &rz, int k, int nwant, double *lb, double *lo)
+{
+    double b = 1e300, l = 1e300;
+    for (int j = 0; j < k; ++j) {
+        const double t = fabs(rz.theta[j]), r = rz.res[j];
+        if (j < nwant || r <= 0.5 * t) {
+            b = std::min(b, t);
+            l = std::min(l, t - r);
+        }
+    }
+    *lb = b;
+    *lo = l;
+}
+
 int modes(Flow &f, double m, char phase, Ritz *rz)
 {
     qs_eig_opts e = f.o.eig;
@@ -86,8 +115,10 @@ int modes(Flow &f, double m, char phase, Ritz *rz)
     r->cg_iterations += st.cg_iterations;
     if (r->n < QS_TRACE_MAX) {
         r->mass[r->n] = m;
-        r->lambda_bar[r->n] = fabs(rz->theta[0]);
-        r->resid[r->n] = rz->res[0];
+        double lb, lo;
+        lambda_bar(*rz, e.k, e.nwant, &lb, &lo);
+        r->lambda_bar[r->n] = lb;
+        r->resid[r->n] = lb - lo;
         r->phase[r->n] = phase;
     }
     if (f.o.window_trace && r->n < f.o.max_steps)
@@ -107,7 +138,8 @@ Window window_of(const Ritz &rz, int k)
 }
 
 // dm proposed by the step model from the last 8 step-A windows (newest first,
-// divided by the newest lambda_bar), clamped to [lb / 2, 8 lb]
+// divided by the newest lambda_bar), clamped to [c lb, 8 lb]: a proposal can only
+// lengthen the plain step of Sec. 3, never shorten it
 int propose(Flow &f, double lb, double *dm)
 {
     float x[8 * QS_WINDOW];
@@ -121,7 +153,7 @@ int propose(Flow &f, double lb, double *dm)
     float y0 = 0.f;
     QS_CUDA(cudaMemcpyAsync(&y0, f.dY, sizeof(float), cudaMemcpyDeviceToHost, st));
     QS_CUDA(cudaStreamSynchronize(st));
-    double ly = std::min(std::max((double)y0, log(0.5)), log(8.0));
+    double ly = std::min(std::max((double)y0, log(f.o.c)), log(8.0));
     *dm = lb * exp(ly);
     return QS_OK;
 }
@@ -162,24 +194,30 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
     };
 
     double m = m_target;
+    const int kk = f.o.eig.k, nw = f.o.eig.nwant;
     Ritz cur;
     st = modes(f, m, 'A', &cur);
     if (st != QS_OK) return finish(st);
-    if (fabs(cur.theta[0]) - cur.res[0] <= 0) return finish(QS_EUNDECIDED);
+    {
+        double lb0, lo0;
+        lambda_bar(cur, kk, nw, &lb0, &lo0);
+        if (!(lo0 > 0)) { rep->fail_reason = 6; return finish(QS_EUNDECIDED); }
+    }
     long flips = 0;
     while (f.steps < f.o.max_steps) {
         // ---- step A -------------------------------------------------------------
         bool go_b = false;
         while (f.steps < f.o.max_steps) {
-            double lb = fabs(cur.theta[0]), rb = cur.res[0];
-            if (!(lb - rb > 0)) { rep->fail_reason = 6; return finish(QS_EUNDECIDED); }
-            // step 4; also stop once the no-crossing interval (m - lb, m + lb) of
+            double lb, lo;
+            lambda_bar(cur, kk, nw, &lb, &lo);
+            if (!(lo > 0)) { rep->fail_reason = 6; return finish(QS_EUNDECIDED); }
+            // step 4; also stop once the no-crossing interval (m - lo, m + lo) of
             // eq. derivativebound already reaches past m0_max
-            if (m > m0max || m + (lb - rb) > m0max) {
+            if (m > m0max || m + lo > m0max) {
                 *sign = (flips % 2 == 0) ? 1 : -1;
                 return finish(QS_OK);
             }
-            f.hist.push_back(window_of(cur, f.o.eig.k));
+            f.hist.push_back(window_of(cur, kk));
             double mn = m + f.o.c * lb;              // step 5
             bool learned = false;
             if (f.o.step_model) {
@@ -189,24 +227,38 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
                 mn = m + dm;
                 learned = true;
             }
-            Ritz nw;
-            st = modes(f, mn, 'A', &nw);
+            Ritz nw_r;
+            st = modes(f, mn, 'A', &nw_r);
             if (st != QS_OK) return finish(st);
             ++f.steps;
-            double lb2 = fabs(nw.theta[0]), rb2 = nw.res[0];
-            bool certified = (lb - rb) + (lb2 - rb2) >= (mn - m);
+            double lb2, lo2;
+            lambda_bar(nw_r, kk, nw, &lb2, &lo2);
+            bool certified = lo + lo2 >= (mn - m);
             if (learned) { if (certified) rep->learned_accepted++; else rep->learned_rejected++; }
-            if (!certified) {
-                // the step left part of [m, mn] outside both crossing-free intervals:
-                // retreat to the edge of the one around m
-                mn = m + 0.95 * (lb - rb);
-                st = modes(f, mn, 'A', &nw);
+            if (learned && !certified) {
+                // the plain rule is the fallback: take the step of Sec. 3 instead
+                mn = m + f.o.c * lb;
+                st = modes(f, mn, 'A', &nw_r);
                 if (st != QS_OK) return finish(st);
                 ++f.steps;
-                lb2 = fabs(nw.theta[0]);
+                lambda_bar(nw_r, kk, nw, &lb2, &lo2);
+                certified = lo + lo2 >= (mn - m);
+            }
+            if (!certified) {
+                // With exact eigenvalues and c < 2 this happens only when lambda_bar
+                // decreased, i.e. at step 3.  The flow is certified up to m: step B
+                // starts there (cur is still the window at m).
+                if (!f.o.retreat) { go_b = true; break; }
+                // retreat option: shorten the step to the edge of the crossing-free
+                // interval around m instead
+                mn = m + 0.95 * lo;
+                st = modes(f, mn, 'A', &nw_r);
+                if (st != QS_OK) return finish(st);
+                ++f.steps;
+                lambda_bar(nw_r, kk, nw, &lb2, &lo2);
             }
             m = mn;
-            cur = nw;
+            cur = nw_r;
             if (lb2 < lb) { go_b = true; break; }   // step 3: lambda_bar decreases
         }
         if (!go_b) break;
@@ -221,7 +273,6 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
         // mass leaves the step uncertified (QS_ENOCONV).  Values are counted over the
         // converged prefix (ended at a gap of the window); for the gap above it the guard
         // values beyond it must lie certainly above a at both masses.
-        const int kk = f.o.eig.k;
         // prefix size: end the prefix at the widest relative gap of the window, among
         // sizes 2 .. 3k/4, so it never cuts into a cluster
         auto pick_prefix = [&](const Ritz &rz) {
@@ -238,7 +289,7 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
         };
         f.nb = pick_prefix(cur);
         int nb = f.nb;
-        // the window at the start mass was solved for step A (few values converged):
+        // the window at the start mass m was solved for step A (few values converged):
         // solve it again (warm) for the step-B prefix
         st = modes(f, m, 'B', &cur);
         if (st != QS_OK) return finish(st);
@@ -289,7 +340,8 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
             };
             int before, sb, ab, after, sa, aa;
             count_below(cur, &before, &sb, &ab);
-            double lb_old = fabs(cur.theta[0]);
+            double lb_old, lo_old;
+            lambda_bar(cur, kk, nb, &lb_old, &lo_old);
             m += dm;
             st = modes(f, m, 'B', &cur);
             if (st != QS_OK) return finish(st);
@@ -300,7 +352,9 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
             if (d % 2) { rep->fail_reason = 4; return finish(QS_ENUMERIC); }   // pairs must stay paired
             flips += d / 2;
             rep->crossings += abs(d) / 2;
-            if (fabs(cur.theta[0]) > lb_old) break;  // lambda_bar grows again: step A
+            double lb_new, lo_new;
+            lambda_bar(cur, kk, nb, &lb_new, &lo_new);
+            if (lb_new > lb_old) break;  // lambda_bar grows again: step A
             f.nb = nb = pick_prefix(cur);
         }
     }

@@ -165,8 +165,7 @@ static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *
     } else {
         CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
         QS_TRY(opQ(lat, w, QS_F32, m0, w->blk32[0], w->blk32[1], k));
-        CK(cudaMemsetAsync(w->blk64[1], 0, (size_t)k * w->nr * sizeof(double), st));
-        CK(qs_axpy_f2d(w->blk64[1], w->blk32[1], DS(w, S_ONES), k, w->nr, st));
+        CK(qs_f2d(w->blk32[1], w->blk64[1], k, w->nr, st));
     }
     const int lowp = prec == QS_F32;
     CK(qs_gram(w->blk64[1], k, w->blk64[1], k, w->nr, w->part, w->Hm, st, lowp));
@@ -182,6 +181,7 @@ static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *
     CK(cudaMemcpyAsync(w->hp + 64 * S_RN, DS(w, S_RN), k * sizeof(double), cudaMemcpyDeviceToHost, st));
     QS_TRY(sync_read(lat, w, S_TMP, k));
     if (w->hi[64] || w->hi[65]) return QS_ENUMERIC;   // Cholesky-QR broke down
+    if (w->hi[66] || w->hi[67]) return QS_ENOCONV;    // Jacobi hit its sweep cap
     double th[64], rs[64], key[64];
     rz->mu_max = 0;
     for (int i = 0; i < k; ++i) {
@@ -203,26 +203,31 @@ static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *
     return QS_OK;
 }
 
-// Chebyshev filter of degree d on Q^2 over [a, b], FP32: blk32[0] (in) -> result
-// in *res (one of blk32); scaled three-term recurrence (values at 0 kept O(1))
-static int cheb_filter(qs_lattice *lat, Workspace *w, double m0, int k, int d, double a, double b, float **res)
+// Chebyshev filter of degree d on Q^2 over [a, b] with FP32 arithmetic: blk32[0] (in)
+// -> result in *res (one of blk32), scaled three-term recurrence (values at 0 kept
+// O(1)).  Each degree is two operator launches: T = Q Y, then the second one computes
+// Y_new = s1 (Q T - c Y) - s2 Y_old in its epilogue.  storage: QS_D32_F32_TILED, or a
+// 16-bit storage whose vectors (52 B per site) live in the same FP32 blocks.
+static int cheb_filter(qs_lattice *lat, Workspace *w, double m0, int k, int d, double a, double b, int storage,
+                       void **res)
 {
-    cudaStream_t st = lat->stream;
-    float *X = w->blk32[0], *Y = w->blk32[1], *Yn = w->blk32[2], *T = w->blk32[3], *AY = w->blk32[4];
-    int64_t n = (int64_t)k * w->nr;
+    void *X = w->blk32[0], *Y = w->blk32[1], *Yn = w->blk32[2], *T = w->blk32[3];
+    double m[QS_MAX_RHS];
+    for (int r = 0; r < k; ++r) m[r] = m0;
     double e = 0.5 * (b - a), c = 0.5 * (b + a);
     double sigma1 = e / (0.0 - c);
     double sigma = sigma1, g = 2.0 / sigma1;
-    QS_TRY(opQ2(lat, w, QS_F32, m0, X, T, AY, k));
-    CK(qs_cheb_step<float>(Y, AY, X, X, c, sigma1 / e, 0.0, n, st));
+    QS_TRY(qs_d32_run(lat, storage, m, X, T, k, 1));
+    QS_TRY(qs_d32_run(lat, storage, m, T, Y, k, 1, X, X, c, sigma1 / e, 0.0));
+    w->f32_count += 2 * k;
     for (int i = 2; i <= d; ++i) {
         double s2 = 1.0 / (g - sigma);
-        QS_TRY(opQ2(lat, w, QS_F32, m0, Y, T, AY, k));
-        CK(qs_cheb_step<float>(Yn, AY, Y, X, c, 2.0 * s2 / e, sigma * s2, n, st));
-        float *tmp = X; X = Y; Y = Yn; Yn = tmp;
+        QS_TRY(qs_d32_run(lat, storage, m, Y, T, k, 1));
+        QS_TRY(qs_d32_run(lat, storage, m, T, Yn, k, 1, Y, X, c, 2.0 * s2 / e, sigma * s2));
+        w->f32_count += 2 * k;
+        void *tmp = X; X = Y; Y = Yn; Yn = tmp;
         sigma = s2;
     }
-    // keep the buffer roles consistent for the caller: result pointer
     *res = Y;
     return QS_OK;
 }
@@ -361,6 +366,12 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
     // ||hopping|| <= 4 (each direction is a partial isometry pair of norm 1)
     double qn = fabs(4.0 + m0) + lat->clov_norm + 4.0;
     double b = qn * qn;
+    // Relative residual with an absolute floor: a pair with r <= atol counts as converged
+    // whatever its theta, so an exact zero mode (|lambda| below any relative accuracy)
+    // still ends the iteration, with |theta| - r <= 0 telling the caller it is undecided.
+    const double atol = 1e-13 * qn;
+    const double theta_floor = atol / o->tol;
+    auto rel = [&](int i) { return rz->res[i] / std::max(fabs(rz->theta[i]), theta_floor); };
     int it = 0, nf = 0, nref = 0;
     *conv = 0;
     double prev_worst = 1e300;
@@ -368,8 +379,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
     int last_prec = plain ? QS_F64 : QS_F32;
     for (it = 0; it < o->max_iter; ++it) {
         double worst = 0;
-        for (int i = 0; i < o->nwant; ++i)
-            worst = std::max(worst, rz->res[i] / std::max(fabs(rz->theta[i]), 1e-300));
+        for (int i = 0; i < o->nwant; ++i) worst = std::max(worst, rel(i));
         // Filter while it makes progress and the block is far from converged; then
         // power steps with Q^-2, whose rate (lambda_i / lambda_{k+1})^2 does not
         // depend on how small lambda_bar is.  The FP32 filter cannot improve a block
@@ -384,9 +394,9 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             double2 P[64 * 64];
             for (int i = 0; i < k * k; ++i) P[i] = make_double2(0, 0);
             for (int i = 0; i < k; ++i)
-                if (rz->res[i] <= o->tol * fabs(rz->theta[i])) P[rz->col[i] * k + nconv++] = make_double2(1, 0);
+                if (rel(i) <= o->tol) P[rz->col[i] * k + nconv++] = make_double2(1, 0);
             for (int i = 0, j = nconv; i < k; ++i)
-                if (!(rz->res[i] <= o->tol * fabs(rz->theta[i]))) P[rz->col[i] * k + j++] = make_double2(1, 0);
+                if (!(rel(i) <= o->tol)) P[rz->col[i] * k + j++] = make_double2(1, 0);
             CK(cudaMemcpyAsync(w->Ym, P, k * k * sizeof(double2), cudaMemcpyHostToDevice, st));
             CK(qs_rotate(w->blk64[0], k, w->Ym, k, w->nr, w->blk64[2], st));
             std::swap(w->blk64[0], w->blk64[2]);
@@ -420,11 +430,14 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             if (plain) {
                 QS_TRY(cheb_filter64(lat, w, m0, k, std::max(2, o->cheb_degree), a, b));
             } else {
-                CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
-                float *Y = nullptr;
-                QS_TRY(cheb_filter(lat, w, m0, k, std::max(2, o->cheb_degree), a, b, &Y));
-                CK(cudaMemsetAsync(w->blk64[2], 0, (size_t)k * w->nr * sizeof(double), st));
-                CK(qs_axpy_f2d(w->blk64[2], Y, DS(w, S_ONES), k, w->nr, st));
+                const int storage = o->precision == QS_F16 ? QS_D32_F16
+                                  : o->precision == QS_BF16 ? QS_D32_BF16 : QS_D32_F32_TILED;
+                if (storage == QS_D32_F32_TILED) CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
+                else CK(qs_q16_from_f64(storage, w->blk64[0], w->blk32[0], lat->g.Ns, k, st));
+                void *Y = nullptr;
+                QS_TRY(cheb_filter(lat, w, m0, k, std::max(2, o->cheb_degree), a, b, storage, &Y));
+                if (storage == QS_D32_F32_TILED) CK(qs_f2d((const float *)Y, w->blk64[2], k, w->nr, st));
+                else CK(qs_f64_from_q16(storage, Y, w->blk64[2], lat->g.Ns, k, st));
                 std::swap(w->blk64[0], w->blk64[2]);
             }
             ++nf;
@@ -451,8 +464,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, last_prec == QS_F32));
         QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, last_prec));
         double nw = 0;
-        for (int i = 0; i < o->nwant; ++i)
-            nw = std::max(nw, rz->res[i] / std::max(fabs(rz->theta[i]), 1e-300));
+        for (int i = 0; i < o->nwant; ++i) nw = std::max(nw, rel(i));
         if (refine) { if (nw > 0.97 * prev_worst) ++stall; else stall = 0; }
         else { if (nw > 0.9 * prev_worst) ++fstall; else fstall = 0; }
         prev_worst = nw;
@@ -478,7 +490,7 @@ extern "C" int qs_lowmodes_at_mass(qs_lattice *lat, double m0, const qs_eig_opts
     qs_eig_opts o;
     if (opts) o = *opts; else qs_eig_default_opts(&o);
     if (o.k < 2 || o.k > 64 || (o.k & 1) || o.nwant < 1 || o.nwant > o.k || !(o.tol > 0) || o.max_iter < 0 ||
-        o.cheb_degree < 2 || (o.precision != QS_F32 && o.precision != QS_F64))
+        o.cheb_degree < 2 || o.precision < QS_F64 || o.precision > QS_BF16)
         return QS_EINVAL;
     if (12 * lat->g.Ns < o.k) return QS_EINVAL;
     CK(cudaSetDevice(lat->device));

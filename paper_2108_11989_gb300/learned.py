@@ -7,16 +7,20 @@ lambda_bar(m_i), zero where missing) -- the same features qs_pfaffian_sign build
 for its proposals -- and the targets are
   y0 = log(dm* / lambda_bar_i), dm* = 0.95 ((lb_i - r_i) + (lb_{i+1} - r_{i+1})),
 the longest step the no-crossing certificate of the observed pair would have
-accepted, and, for each window slot j, whether the signed value changed sign.
+accepted, and, for each of the 24 window slots j, whether the signed value in slot j
+changed sign between the two masses.  So T has 1 + 24 = 25 columns, the output width
+of the step network.
 """
 import numpy as np
 
 WINDOW = 24
 HIST = 8
+N_IN = HIST * WINDOW     # network inputs: 8 windows of 24 scaled eigenvalues
+N_OUT = 1 + WINDOW       # network outputs: log step + one crossing logit per slot
 
 
 def samples_from_flow(report):
-    """(X [n][8*24], T [n][25]) float32 from one flow report with windows."""
+    """(X [n][8*24], T [n][1 + 24]) float32 from one flow report with windows."""
     W = report["windows"]
     ph = report["phase"]
     m = np.asarray(report["mass"])
@@ -35,13 +39,13 @@ def samples_from_flow(report):
         dm = 0.95 * ((lb[i] - r[i]) + (lb[j] - r[j]))
         if not dm > 0:
             continue
-        t = np.zeros(1 + WINDOW - 1)
+        t = np.zeros(N_OUT)
         t[0] = np.log(dm / lb[i])
-        t[1:] = (np.sign(W[i][:WINDOW - 1]) * np.sign(W[j][:WINDOW - 1]) < 0).astype(float)
+        t[1:] = (np.sign(W[i][:WINDOW]) * np.sign(W[j][:WINDOW]) < 0).astype(float)
         X.append(x.ravel())
         T.append(t)
     if not X:
-        return np.zeros((0, HIST * WINDOW), np.float32), np.zeros((0, WINDOW), np.float32)
+        return np.zeros((0, N_IN), np.float32), np.zeros((0, N_OUT), np.float32)
     return np.asarray(X, np.float32), np.asarray(T, np.float32)
 
 

@@ -43,11 +43,16 @@ def gell_mann():
 
 
 def random_su3_field(rng, T, L, eps):
-    """exp(i eps H) per link, H Gaussian traceless Hermitian (see module doc)."""
+    """exp(i eps H) per link, H Gaussian traceless Hermitian (see module doc).  All
+    h_a are drawn first; the exponentials are then formed one time slice at a time
+    (the same numbers as all at once, with bounded memory)."""
     h = rng.standard_normal((T, L, L, L, 4, 8))
-    H = np.einsum("...a,aij->...ij", h, gell_mann()) / 2.0
-    w, v = np.linalg.eigh(H)
-    U = np.einsum("...ik,...k,...jk->...ij", v, np.exp(1j * eps * w), v.conj())
+    G = gell_mann()
+    U = np.empty((T, L, L, L, 4, 3, 3), dtype=np.complex128)
+    for t in range(T):
+        H = np.einsum("...a,aij->...ij", h[t], G) / 2.0
+        w, v = np.linalg.eigh(H)
+        U[t] = np.einsum("...ik,...k,...jk->...ij", v, np.exp(1j * eps * w), v.conj())
     return U
 
 
@@ -86,10 +91,28 @@ class GaugeConfig:
 
 
 def make_config(T, L, eps, theta_sigma=0.0, csw_su3=1.5, csw_u1=0.0, seed=0,
-                t_antiperiodic=False, cstar_mask=0b111):
+                t_antiperiodic=False, cstar_mask=0b111, cache_dir=None):
+    """A seeded synthetic configuration.  cache_dir (or the environment variable
+    QS_FIELD_CACHE): keep the drawn links and angles there as .npy files and reuse them
+    (large lattices take a minute to draw)."""
+    import os
+    cache_dir = cache_dir or os.environ.get("QS_FIELD_CACHE")
+    path = None
+    if cache_dir:
+        tag = f"T{T}_L{L}_eps{eps!r}_th{theta_sigma!r}_seed{seed}"
+        path = os.path.join(cache_dir, tag)
+        if os.path.exists(path + "_su3.npy"):
+            su3 = np.load(path + "_su3.npy")
+            theta = np.load(path + "_theta.npy") if os.path.exists(path + "_theta.npy") else None
+            return GaugeConfig(T, L, su3, theta, csw_su3, csw_u1, t_antiperiodic, cstar_mask)
     rng = np.random.default_rng(seed)
     su3 = random_su3_field(rng, T, L, eps)
     theta = random_u1_field(rng, T, L, theta_sigma) if theta_sigma > 0 else None
+    if path:
+        os.makedirs(cache_dir, exist_ok=True)
+        np.save(path + "_su3.npy", su3)
+        if theta is not None:
+            np.save(path + "_theta.npy", theta)
     return GaugeConfig(T, L, su3, theta, csw_su3, csw_u1, t_antiperiodic, cstar_mask)
 
 

@@ -162,8 +162,8 @@ def test_tiled_layout_matches_canonical(qs, prec, nrhs):
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
 def test_batched_configs_of_uneven_volume(qs, prec, tol):
-    """qs_apply_Q_batch: three configurations of different volumes, a mass per
-    right-hand side, in one launch = qs_apply_Q on each vector separately."""
+    """qs_apply_Q_batch in the canonical layout (FP64: the FP64 batched kernel; FP32: the
+    persistent FP32 one) = qs_apply_Q on each vector at its own mass."""
     import torch
     dt = torch.float64 if prec == "f64" else torch.float32
     cfgs = [make_config(T=4, L=4, eps=0.4, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=31),
@@ -188,5 +188,111 @@ def test_batched_configs_of_uneven_volume(qs, prec, tol):
     torch.cuda.synchronize()
     for (_, _, y, _), ref in zip(items, refs):
         assert (y - ref).abs().max().item() <= tol * ref.abs().max().item()
+    for lat in lats:
+        lat.close()
+
+
+# ---- 16-bit spinor storage (tiled, per-site FP32 scale), FP32 arithmetic ----------
+# Tolerances (max-norm, relative to the largest output component): the output is
+# rounded to 16 bits relative to its site's largest component, so the error is at most
+# half a unit in the last place of the 16-bit format at 1.0 (2^-11 for FP16, 2^-8 for
+# BF16) plus FP32 arithmetic; the tests allow twice that.
+TOL16 = {"f16": 2 * 2.0 ** -11, "bf16": 2 * 2.0 ** -8}
+
+
+def pack16(psi, kind):
+    """complex [nrhs][Ns][12] -> uint8 tiles (12 x 16 words of two 16-bit reals, then 16
+    FP32 scales per 16 sites) and the values the format represents (complex128)."""
+    import torch
+    nr, ns = psi.shape[0], psi.shape[1]
+    re = np.stack([psi.real, psi.imag], axis=-1)                        # [nr][ns][12][2]
+    scale = np.abs(re).reshape(nr, ns, 24).max(axis=2).astype(np.float32)
+    q = re / np.where(scale > 0, scale, 1.0)[:, :, None, None]
+    t = torch.from_numpy(q.astype(np.float32))
+    h = t.to(torch.float16 if kind == "f16" else torch.bfloat16)
+    deq = h.to(torch.float32).numpy().astype(np.float64) * scale[:, :, None, None]
+    words = h.contiguous().view(torch.int16).numpy().reshape(nr, ns // 16, 16, 12, 2)
+    words = words.transpose(0, 1, 3, 2, 4)                               # [nr][tile][12][16][2]
+    buf = np.zeros((nr, ns // 16, 832), dtype=np.uint8)
+    buf[:, :, :768] = np.ascontiguousarray(words).view(np.uint8).reshape(nr, ns // 16, 768)
+    buf[:, :, 768:] = scale.reshape(nr, ns // 16, 16).view(np.uint8).reshape(nr, ns // 16, 64)
+    return buf.reshape(-1), deq[..., 0] + 1j * deq[..., 1]
+
+
+def unpack16(buf, nr, ns, kind):
+    import torch
+    b = buf.reshape(nr, ns // 16, 832)
+    words = np.ascontiguousarray(b[:, :, :768]).view(np.int16).reshape(nr, ns // 16, 12, 16, 2)
+    scale = np.ascontiguousarray(b[:, :, 768:]).view(np.float32).reshape(nr, ns)
+    h = torch.from_numpy(np.ascontiguousarray(words.transpose(0, 1, 3, 2, 4))).view(
+        torch.float16 if kind == "f16" else torch.bfloat16)
+    v = h.to(torch.float32).numpy().astype(np.float64).reshape(nr, ns, 12, 2) * scale[:, :, None, None]
+    return v[..., 0] + 1j * v[..., 1]
+
+
+@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("nrhs", [1, 5])
+def test_16bit_storage_against_oracle(qs, kind, nrhs):
+    import torch
+    # ragged volume (2160 sites = 135 tiles, not a multiple of the 128-thread block)
+    cfg = make_config(T=5, L=6, eps=0.5, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=4, cstar_mask=0b101)
+    lat = qs.Lattice(cfg.L, cfg.T, cfg.cstar_mask)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    ns = cfg.n_sites
+    psi = random_spinor(17, cfg.T, cfg.L, nrhs).reshape(nrhs, ns, 12)
+    psi[:, ::7] *= 1e-3          # sites of very different magnitude
+    buf, deq = pack16(psi, kind)
+    x = torch.from_numpy(buf).cuda()
+    y = torch.zeros_like(x)
+    prec = qs.QS_F16 if kind == "f16" else qs.QS_BF16
+    m0 = -0.21
+    lat.apply_Q(m0, x, y, tiled=True, prec=prec)
+    got = unpack16(y.cpu().numpy(), nrhs, ns, kind)
+    op = WilsonDirac(cfg)
+    for r in range(nrhs):
+        ref = op.apply_Q(deq[r].reshape(-1), m0).reshape(ns, 12)
+        err = np.abs(got[r] - ref).max() / np.abs(ref).max()
+        assert err <= TOL16[kind], (kind, r, err)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_batched_configs_against_oracle(qs, prec):
+    """qs_apply_Q_batch (one persistent launch over three configurations of uneven volume,
+    a mass per right-hand side) against the oracle's apply_Q at each mass."""
+    import torch
+    cfgs = [make_config(T=4, L=4, eps=0.4, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=31),
+            make_config(T=6, L=4, eps=0.3, theta_sigma=0.2, csw_su3=1.9, csw_u1=1.0, seed=32),
+            make_config(T=4, L=6, eps=0.2, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=33)]
+    masses = [[-0.3, 0.1], [0.05, -0.2, 0.4], [0.0]]
+    lats, items, keep = [], [], []
+    for cfg, ms in zip(cfgs, masses):
+        lat = qs.Lattice(cfg.L, cfg.T)
+        lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+        nr, ns = len(ms), cfg.n_sites
+        psi = random_spinor(7 + nr, cfg.T, cfg.L, nr).reshape(nr, ns, 12)
+        if prec == "f32":
+            x = _to_dev(psi.astype(np.complex64).astype(np.complex128), torch.float32).reshape(-1)
+            x = qs.to_tiled(x, ns)
+            inp = psi.astype(np.complex64).astype(np.complex128)
+        else:
+            buf, inp = pack16(psi, "f16")
+            x = torch.from_numpy(buf).cuda()
+        y = torch.zeros_like(x)
+        lats.append(lat)
+        items.append((lat, x, y, ms))
+        keep.append((cfg, inp, nr, ns))
+    qs.apply_Q_batch(items, tiled=True, prec=qs.QS_F32 if prec == "f32" else qs.QS_F16)
+    torch.cuda.synchronize()
+    for (lat, x, y, ms), (cfg, inp, nr, ns) in zip(items, keep):
+        if prec == "f32":
+            got = _from_dev(qs.from_tiled(y, ns), (nr, ns, 12))
+        else:
+            got = unpack16(y.cpu().numpy(), nr, ns, "f16")
+        op = WilsonDirac(cfg)
+        for r, m in enumerate(ms):
+            ref = op.apply_Q(inp[r].reshape(-1), m).reshape(ns, 12)
+            err = np.abs(got[r] - ref).max() / np.abs(ref).max()
+            assert err <= (TOL["f32"] if prec == "f32" else TOL16["f16"]), (prec, r, err)
     for lat in lats:
         lat.close()

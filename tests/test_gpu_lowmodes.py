@@ -99,3 +99,28 @@ def test_plain_fp64_form_matches(qs):
     check_against(ev, rs, ref, 8)
     assert st["dslash_f32"] == 0 and st["refine_passes"] == 0
     lat.close()
+
+
+@pytest.mark.parametrize("precision", [2, 3])   # QS_F16, QS_BF16 filter storage
+def test_16bit_filter_storage_keeps_fp64_accuracy(qs, precision):
+    """The filter's vectors in 16 bits (per-site scale): the FP64 Rayleigh-Ritz and the
+    mixed refinement still give the dense oracle's low eigenvalues to 1e-10."""
+    cfg = make_config(T=4, L=2, eps=0.9, theta_sigma=0.4, csw_su3=1.3, csw_u1=0.8, seed=5)
+    lat = lattice(qs, cfg)
+    opts = qs.eig_default_opts(k=16, nwant=8, tol=1e-9, cheb_degree=16, precision=precision)
+    ev, rs, st = lat.lowmodes_at_mass(-0.6, opts)
+    ref = np.linalg.eigvalsh(WilsonDirac(cfg).dense_Q(-0.6))
+    check_against(ev, rs, ref, 8)
+    assert st["filter_passes"] > 0
+    lat.close()
+
+
+def test_16bit_filter_on_tiny_workload_golden(qs):
+    g = json.load(open(os.path.join(HERE, "golden", "tiny_4x4x4x4_seed0.json")))
+    cfg = make_config(seed=0, **WORKLOADS["tiny_4x4x4x4"])
+    lat = lattice(qs, cfg)
+    opts = qs.eig_default_opts(k=16, nwant=8, tol=1e-9, cheb_degree=24, precision=2)
+    pt = g["points"][0]
+    ev, rs, st = lat.lowmodes_at_mass(pt["m0"], opts)
+    check_against(ev, rs, np.array(pt["lowest_abs_sorted_eigs_Q"]), 8)
+    lat.close()

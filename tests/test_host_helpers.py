@@ -41,8 +41,11 @@ def test_samples_from_flow():
     rep = {"windows": W, "phase": "AAAB", "mass": [0.0, 0.19, 0.57, 0.6],
            "lambda_bar": [0.1, 0.2, 0.4, 0.35], "resid": [0.0, 0.0, 0.0, 0.0]}
     X, T = samples_from_flow(rep)
-    assert X.shape == (2, 192) and T.shape == (2, 24)
+    assert X.shape == (2, 192) and T.shape == (2, 25)     # 1 step target + 24 crossing labels
     assert np.isclose(T[0, 0], np.log(0.95 * (0.1 + 0.2) / 0.1))
     assert X[0, 0] == np.float32(1.0)               # newest window / its lambda_bar
     assert X[1, 24] == np.float32(0.1 / 0.2)         # previous step-A window, scaled
     assert T[1, 2] == 1.0 and T[0, 2] == 0.0         # slot 1 changes sign between masses 1 and 2
+    W[:, 23] = [0.5, -0.5, -0.5, 0.5]                # the last slot has its own label
+    X, T = samples_from_flow(rep)
+    assert T[0, 24] == 1.0 and T[1, 24] == 0.0

@@ -197,3 +197,38 @@ def test_pfaffian_squared_is_det_D():
     assert np.isclose(ph * ph, sd, atol=1e-9)
     sct, lct = np.linalg.slogdet(op.CT_matrix().toarray())
     assert np.isclose(lct, 0.0, atol=1e-12) and np.isclose(sct, 1.0)
+
+
+@pytest.mark.parametrize("mask,t_anti", [(0b111, False), (0b011, True)])
+def test_plain_loop_c_operator_matches_assembled_one(mask, t_anti):
+    """oracle/dirac_c.c (explicit loops over spin and colour) against the numpy
+    assembly of the same formula, D and Q, on a rough field."""
+    from oracle.dirac import WilsonDiracC
+    cfg = make_config(T=3, L=2, eps=0.8, theta_sigma=0.4, csw_su3=1.3, csw_u1=0.7, seed=9,
+                      t_antiperiodic=t_anti, cstar_mask=mask)
+    a, b = WilsonDirac(cfg), WilsonDiracC(cfg)
+    rng = np.random.default_rng(3)
+    psi = rng.standard_normal(a.n) + 1j * rng.standard_normal(a.n)
+    for m0 in (-0.41, 0.3):
+        assert np.allclose(b.apply_D(psi, m0), a.apply_D(psi, m0), atol=1e-13, rtol=0)
+        assert np.allclose(b.apply_Q(psi, m0), a.apply_Q(psi, m0), atol=1e-13, rtol=0)
+
+
+def test_plain_loop_c_operator_free_field_and_hermiticity():
+    from oracle.dirac import WilsonDiracC
+    from oracle.gamma import GAMMA
+    T, L = 4, 4
+    op = WilsonDiracC(free_cfg(T, L))
+    lat = op.lat
+    m0 = -0.23
+    for p in cstar_momenta(T, L)[[5, 77, 300]]:
+        u = np.arange(12).reshape(4, 3) + 1j
+        phase = np.exp(1j * (p[0] * lat.t + p[1] * lat.x + p[2] * lat.y + p[3] * lat.z))
+        psi = phase[:, None, None] * u[None]
+        Dp = (m0 + np.sum(1 - np.cos(p))) * np.eye(4) + 1j * sum(GAMMA[m] * np.sin(p[m]) for m in range(4))
+        assert np.allclose(op.apply_D(psi.reshape(-1), m0), (phase[:, None, None] * (Dp @ u)[None]).reshape(-1),
+                           atol=1e-12)
+    rough = WilsonDiracC(rough_cfg(T=4, L=2))
+    rng = np.random.default_rng(8)
+    f, g = (rng.standard_normal(rough.n) + 1j * rng.standard_normal(rough.n) for _ in range(2))
+    assert np.isclose(np.vdot(f, rough.apply_Q(g, 0.2)), np.vdot(rough.apply_Q(f, 0.2), g), rtol=1e-12)

@@ -1,0 +1,39 @@
+"""Pins of oracle/evenodd.py (Sec. 4: D^oo, W_eo, the even-odd Schur complement)."""
+import numpy as np
+import pytest
+
+from synth_inputs import GaugeConfig, make_config, unit_su3_field
+from oracle.dirac import WilsonDirac
+from oracle.evenodd import log_det_oo, parity, schur_det, w_eo
+
+
+@pytest.fixture(scope="module")
+def rough():
+    cfg = make_config(T=4, L=2, eps=0.9, theta_sigma=0.4, csw_su3=1.3, csw_u1=0.8, seed=5)
+    return WilsonDirac(cfg)
+
+
+def test_odd_odd_part_is_site_diagonal_and_matches_blocks(rough):
+    D = rough.dense_D(-0.4)
+    p = np.repeat(parity(rough.lat), 12)
+    o = np.nonzero(p == 1)[0]
+    Doo = D[np.ix_(o, o)]
+    site = o // 12
+    off_site = site[:, None] != site[None, :]
+    assert np.max(np.abs(Doo[off_site])) == 0.0          # no hopping between odd sites
+    assert np.isclose(np.linalg.slogdet(Doo)[1], log_det_oo(rough, -0.4), rtol=1e-12)
+
+
+def test_schur_identity(rough):
+    loo, lhat, ld = schur_det(rough, 0.25)
+    assert np.isclose(loo + lhat, ld, rtol=1e-11)
+    assert np.isclose(loo, log_det_oo(rough, 0.25), rtol=1e-12)
+
+
+def test_free_field_closed_form():
+    T, L = 4, 2
+    op = WilsonDirac(GaugeConfig(T, L, unit_su3_field(T, L), None, 1.9, 1.0))
+    n_odd = op.lat.n_sites // 2
+    for m0 in (-0.3, 0.7):
+        assert np.isclose(log_det_oo(op, m0), 12 * n_odd * np.log(abs(4.0 + m0)), rtol=1e-13)
+    assert np.isclose(w_eo(op, -0.3, 0.7), (4.7 / 3.7) ** (6 * n_odd), rtol=1e-12)

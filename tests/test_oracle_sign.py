@@ -48,14 +48,56 @@ def test_three_routes_agree(rough):
     assert -1 in signs and 1 in signs
 
 
-def test_flow_matches_definition(rough):
+@pytest.mark.parametrize("retreat", [False, True])
+def test_flow_matches_definition(rough, retreat):
     op, pairs = rough
     for m in [-2.05, -1.65, -1.5, 0.3]:
-        s, rep = pfaffian_sign_flow(lambda mm: modes_dense(op, mm, 24), m, m0_max_default(op.cfg))
-        assert s == sign_from_real_eigs(pairs, m), m
+        s, rep = pfaffian_sign_flow(lambda mm: modes_dense(op, mm, 24), m, m0_max_default(op.cfg),
+                                    retreat=retreat)
+        assert s == sign_from_real_eigs(pairs, m), (m, retreat)
     for m in [-1.65, -1.5]:
-        s2, _ = pfaffian_sign_flow(lambda mm: modes_sparse(op, mm, 16), m, m0_max_default(op.cfg))
+        s2, _ = pfaffian_sign_flow(lambda mm: modes_sparse(op, mm, 16), m, m0_max_default(op.cfg),
+                                   retreat=retreat)
         assert s2 == sign_from_real_eigs(pairs, m)
+
+
+def test_flow_step_a_follows_the_enumerated_algorithm(rough):
+    """Paper order (Sec. 3): while lambda_bar grows every step-A step is exactly
+    c lambda_bar; the first decrease hands over to step B, which starts from a mass
+    whose crossing-free interval reaches the next mass visited."""
+    op, _ = rough
+    c = 1.9
+    s, rep = pfaffian_sign_flow(lambda mm: modes_dense(op, mm, 24), -1.65, m0_max_default(op.cfg), c=c)
+    m, lb, ph = rep["masses"], rep["lambda_bar"], rep["phase"]
+    assert "B" in ph
+    i = 0
+    while ph[i + 1] == "A":
+        assert m[i + 1] > m[i]
+        if lb[i + 1] < lb[i]:
+            break
+        assert np.isclose(m[i + 1] - m[i], c * lb[i], rtol=1e-12)     # step 5
+        i += 1
+    # the first B mass continues from a certified mass: within lambda_bar of one of the
+    # step-A masses before it, above it
+    j = ph.index("B")
+    starts = [k for k in range(j) if m[k] < m[j] and m[j] - m[k] <= lb[k] + 1e-12]
+    assert starts
+
+
+def test_flow_retreat_option_shortens_uncovered_steps():
+    """A window function that makes lambda_bar collapse after the first step: the paper
+    order goes to step B from the first mass; the retreat option first tries the edge
+    of the crossing-free interval, m0 + 0.95 lambda_bar."""
+    def modes(m):      # a pair +-lambda that dips to 1e-3 at m = 1 + 0.95 * 1.002
+        lam = abs(0.5 - 0.5253 * (m - 1.0)) + 1e-3
+        w = np.array([lam, -lam, 3.0, -3.0, 4.0, -4.0])
+        return w, np.zeros(6)
+    s0, r0 = pfaffian_sign_flow(modes, 1.0, 3.0, max_steps=50)
+    s1, r1 = pfaffian_sign_flow(modes, 1.0, 3.0, max_steps=50, retreat=True)
+    assert s0 == s1 == 1
+    assert r0["phase"][:3] == ["A", "A", "B"] and r0["masses"][2] > 1.0
+    assert r1["phase"][:4] == ["A", "A", "A", "B"]
+    assert np.isclose(r1["masses"][2], 1.0 + 0.95 * 0.501)
 
 
 def test_large_mass_positive(rough):
@@ -87,4 +129,27 @@ def test_lowmodes_sparse_vs_dense(rough):
     wd, _ = modes_dense(op, -1.3, 8)
     ws, rs = modes_sparse(op, -1.3, 8)
     assert np.allclose(np.sort(wd), np.sort(ws), atol=1e-10)
+    assert np.all(rs < 1e-9)
+
+
+def test_lowmodes_sparse_free_field_closed_form():
+    """modes_sparse on a free 2^3 x 6 field (n = 1152): the 12 eigenvalues nearest zero
+    equal the closed-form C* spectrum +-sqrt(M(p)^2 + sum sin^2 p) (Sec. 2 operator)."""
+    from synth_inputs import GaugeConfig, unit_su3_field
+    T, L, m0 = 6, 2, -0.35
+    op = WilsonDirac(GaugeConfig(T, L, unit_su3_field(T, L), None, 1.9, 1.0))
+    ev = []
+    for n1 in range(2 * L):
+        p1 = np.pi * n1 / L
+        for n2 in range(L):
+            for n3 in range(L):
+                for n0 in range(T):
+                    p = np.array([2 * np.pi * n0 / T, p1, p1 + 2 * np.pi * n2 / L, p1 + 2 * np.pi * n3 / L])
+                    M = m0 + np.sum(1 - np.cos(p))
+                    e = np.sqrt(M * M + np.sum(np.sin(p) ** 2))
+                    ev += [e] * 6 + [-e] * 6
+    ev = np.array(ev)
+    ref = np.sort(np.abs(ev))[:12]
+    ws, rs = modes_sparse(op, m0, 12)
+    assert np.allclose(np.sort(np.abs(ws)), ref, atol=1e-10)
     assert np.all(rs < 1e-9)

@@ -29,7 +29,9 @@ def test_noalloc_matches_apply_Q_on_two_calls(prec, tol):
         lat.apply_Q(m0, x, ref)
         out = torch.full_like(x, float("nan"))
         nrm = torch.full((nrhs,), float("nan"), dtype=torch.float64, device="cuda")
+        n0 = qs.kernel_launches()
         qs.apply_Q_norm2_noalloc(lat.h, m0, x, out, nrm)
+        assert qs.kernel_launches() - n0 == 3     # the operator and the two-stage norm
         torch.cuda.synchronize()
         a, b = out.double().cpu().numpy(), ref.double().cpu().numpy()
         assert np.abs(a - b).max() <= tol * np.abs(b).max()
