@@ -28,7 +28,8 @@
  *   process.  On error the contents of output buffers are unspecified.
  *   qs_strerror() gives a static message.
  * Streams.  All GPU work of a lattice handle runs on the stream given at creation
- *   (NULL = the legacy default stream).  Calls on one handle must not overlap.
+ *   (NULL = the legacy default stream).  Calls on one handle must not overlap; calls on
+ *   different handles may run in different host threads.
  * No CPU fallback: a call that cannot run on the GPU returns QS_ECUDA.
  */
 #ifndef QSTAR_H
@@ -114,6 +115,13 @@ QS_API int qs_apply_Dw(qs_lattice *lat, double m0, const void *in, void *out, in
 /* out = Q(m0) in = gamma_5 D(m0) in (Sec. 3).  Same arguments as qs_apply_Dw. */
 QS_API int qs_apply_Q(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int prec);
 
+/* out = P in = C T gamma_5 in^* for nrhs FP64 spinors (prec = QS_F64, optionally with
+ * QS_LAYOUT_TILED): the antiunitary symmetry of Sec. 3 -- if Q v = lambda v then P v is
+ * an eigenvector with the same eigenvalue, orthogonal to v (the double degeneracy of
+ * the spectrum of Q).  T is the translation by L along x, C = i gamma_0 gamma_2; P
+ * commutes with Q and P^2 = -1.  DEVICE buffers, not overlapping.  Asynchronous. */
+QS_API int qs_cstar_partner(qs_lattice *lat, const void *in, void *out, int nrhs, int prec);
+
 /* Convert nrhs spinors between precisions, both in the tiled layout (in_prec, out_prec:
  * QS_F64, QS_F32, QS_F16, QS_BF16, different; QS_LAYOUT_TILED may be ORed in).  Into 16
  * bits each site is scaled by its largest component; out of 16 bits the values are
@@ -195,6 +203,10 @@ typedef struct {
                           vectors stored in 16 bits (per-site scale, FP32 arithmetic);
                           QS_F64: plain FP64 form (FP64 filter passes and FP64 Rayleigh-Ritz
                           only) */
+    int pairing;       /* 1: in the mixed forms, filter and Q^-2 steps act on k / 2 vectors and
+                          their C* partners C T gamma_5 v^* (qs_cstar_partner) complete the
+                          block -- the spectrum is doubly degenerate (Sec. 3), so half the
+                          operator work spans the same subspace; 0: all k vectors */
 } qs_eig_opts;
 
 typedef struct {
@@ -206,7 +218,7 @@ typedef struct {
 } qs_eig_stats;
 
 /* Fill *opts with defaults (k = 16, nwant = 4, tol = 1e-8, max_iter = 200,
- * cheb_degree = 24, warm_start = 1, seed = 1, precision = QS_F32). */
+ * cheb_degree = 24, warm_start = 1, seed = 1, precision = QS_F32, pairing = 1). */
 QS_API void qs_eig_default_opts(qs_eig_opts *opts);
 
 /* Lowest-|lambda| eigenpairs of Q(m0) on the handle's gauge field.
@@ -307,6 +319,17 @@ QS_API int qs_log_det_oo(qs_lattice *lat, int nmass, const double *m0, double *l
 /* *w_eo = W_eo(m -> mp) and *log_w_eo its logarithm (either may be NULL, not both). */
 QS_API int qs_w_eo(qs_lattice *lat, double m, double mp, double *w_eo, double *log_w_eo);
 
+/* W_sgn for n configurations at once (the batched form; Sec. 3 runs the algorithm on
+ * each configuration independently).  lats: n distinct handles with gauge fields
+ * loaded; m0_targets, signs, status: HOST arrays of n; reports: NULL or n reports.
+ * The flows run concurrently, one host thread each on its handle's stream, so the GPU
+ * overlaps their work -- give every handle its own stream (handles on one stream
+ * serialise).  status[i] receives qs_pfaffian_sign's status for configuration i; the
+ * return value is QS_OK if all succeeded, else the first failing status.  Synchronises
+ * every stream. */
+QS_API int qs_pfaffian_sign_batch(qs_lattice *const *lats, int n, const double *m0_targets,
+                                  const qs_sign_opts *opts, int *signs, int *status, qs_sign_report *reports);
+
 /* ---------------------------------------------------------------------------
  * Kernel profiling (measurement support, no counterpart in the paper).  While on,
  * every operator launch of the handle is bracketed by CUDA events on the handle's
@@ -359,7 +382,7 @@ QS_API int qs_apply_Q_norm2_noalloc(qs_lattice *lat, double m0, const void *in, 
 /* Static description of a status code. */
 QS_API const char *qs_strerror(int status);
 
-/* Text of the last CUDA error seen by the library in this process ("" if none). */
+/* Text of the last CUDA error the library saw in the calling thread ("" if none). */
 QS_API const char *qs_last_cuda_error(void);
 
 #ifdef __cplusplus

@@ -43,7 +43,7 @@ class BatchItem(ctypes.Structure):
 class EigOpts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nwant", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("warm_start", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("precision", ctypes.c_int), ("pairing", ctypes.c_int)]
 
 
 class EigStats(ctypes.Structure):
@@ -111,6 +111,7 @@ def _load():
         "qs_sign_default_opts": (None, [ctypes.POINTER(SignOpts)]),
         "qs_pfaffian_sign": (I, [P, D, ctypes.POINTER(SignOpts), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(SignReport)]),
+        "qs_pfaffian_sign_batch": (I, [P, I, P, ctypes.POINTER(SignOpts), P, P, P]),
         "qs_set_profiling": (I, [P, I]),
         "qs_get_profile": (I, [P, ctypes.POINTER(Profile)]),
         "qs_kernel_launches": (ctypes.c_int64, []),
@@ -125,6 +126,7 @@ def _load():
         "qs_apply_Q_batch": (I, [ctypes.POINTER(BatchItem), I, I, P]),
         "qs_convert_spinors": (I, [P, P, I, P, I, I]),
         "qs_log_det_oo": (I, [P, I, P, P]),
+        "qs_cstar_partner": (I, [P, P, P, I, I]),
         "qs_w_eo": (I, [P, D, D, P, P]),
         "qs_apply_Q_norm2_noalloc": (I, [P, D, P, P, I, I, P]),
         "qs_strerror": (ctypes.c_char_p, [I]),
@@ -285,6 +287,12 @@ def pfaffian_sign(h, m0_target, opts=None, step_model=None, trace=False):
     return sg.value, out
 
 
+def cstar_partner(h, inp, out, tiled=False):
+    """qs_cstar_partner: out = C T gamma_5 conj(in) for float64 device spinors."""
+    _check(_lib.qs_cstar_partner(h, inp.data_ptr(), out.data_ptr(), _nrhs(h, inp),
+                                 QS_F64 | (QS_LAYOUT_TILED if tiled else 0)), "cstar_partner")
+
+
 def log_det_oo(h, masses):
     """qs_log_det_oo: log|det D^oo(m0)| for each bare mass (numpy array)."""
     m = np.ascontiguousarray(masses, dtype=np.float64)
@@ -303,6 +311,24 @@ def w_eo(h, m, mp):
 def convert_spinors(h, inp, in_prec, out, out_prec, nrhs):
     """qs_convert_spinors: tiled spinors from one precision to another (device buffers)."""
     _check(_lib.qs_convert_spinors(h, inp.data_ptr(), in_prec, out.data_ptr(), out_prec, nrhs), "convert_spinors")
+
+
+def pfaffian_sign_batch(lattices, m0_targets, opts=None):
+    """qs_pfaffian_sign_batch: [(sign, status, report dict)] for several lattices at once."""
+    n = len(lattices)
+    hs = (ctypes.c_void_p * n)(*[(l.h if hasattr(l, "h") else l).value for l in lattices])
+    m = np.ascontiguousarray(m0_targets, dtype=np.float64)
+    o = opts if opts is not None else sign_default_opts()
+    o.step_model = None
+    o.window_trace = None
+    signs = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    reps = (SignReport * n)()
+    code = _lib.qs_pfaffian_sign_batch(hs, n, m.ctypes.data, ctypes.byref(o), signs.ctypes.data,
+                                       status.ctypes.data, reps)
+    if code not in (0,) and not np.any(status != 0):
+        _check(code, "pfaffian_sign_batch")
+    return [(int(signs[i]), int(status[i]), reps[i].as_dict()) for i in range(n)]
 
 
 def apply_Q_norm2_noalloc(h, m0, inp, out, norm2):

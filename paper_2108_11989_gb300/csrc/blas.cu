@@ -3,6 +3,7 @@
 // vector, then one fixed-order pass), so results are bit-reproducible.
 #include "blas.cuh"
 
+#include <mutex>
 #include <type_traits>
 
 namespace {
@@ -87,116 +88,166 @@ __global__ void resid_part(const double *__restrict__ a, const double *__restric
     if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
-// Gram partials: each block accumulates G[i][j] over chunks of GCH complex
-// elements staged in shared memory; pair q = i * kb + j, thread owns q = tid + 256 m.
-#define GCH 32
-#define GMAXP 16
-// LOWP: products and the sum over one chunk of GCH elements in FP32, chunk sums
-// accumulated in FP64 (one FP64 add per chunk instead of four FMAs per element)
+// Gram partials G[i][j] = sum_e conj(A_i[e]) B_j[e] (i < ka, j < kb <= 64).  A block
+// stages a chunk of GE elements of all ka + kb vectors in shared memory, element-major
+// ([e][vector], row padded by one complex to spread the banks); each thread owns a 4 x 4
+// tile of (i, j) and a residue class of the chunk's elements, so every staged value it
+// reads feeds four complex multiply-adds.  The element classes of a tile are summed in
+// shared memory at the end, in a fixed order.  LOWP: values rounded to FP32, products
+// and the sum over one chunk in FP32, chunk sums added in FP64.
+#define GE 64
 template <bool LOWP>
-__global__ void __launch_bounds__(256) gram_part(const double *__restrict__ A, int ka,
-                                                 const double *__restrict__ B, int kb, int64_t nc,
-                                                 double *part)
+__global__ void __launch_bounds__(256) gram_tile_kernel(const double2 *__restrict__ A, int ka,
+                                                        const double2 *__restrict__ B, int kb, int64_t nc,
+                                                        double *part)
 {
-    // FP64 staging: double2 [ka + kb][GCH]; FP32 staging (LOWP): float2, converted once
-    // per element when loaded (FP64 -> FP32 conversions run on the FP64 pipe)
-    extern __shared__ double2 gsh[];
-    float2 *gsf = reinterpret_cast<float2 *>(gsh);
-    const double2 *A2 = reinterpret_cast<const double2 *>(A);
-    const double2 *B2 = reinterpret_cast<const double2 *>(B);
-    const int P = ka * kb;
-    double ar[GMAXP], ai[GMAXP];
+    typedef typename std::conditional<LOWP, float2, double2>::type V2;
+    typedef typename std::conditional<LOWP, float, double>::type T;
+    extern __shared__ __align__(16) unsigned char gsm_raw[];
+    V2 *sv = reinterpret_cast<V2 *>(gsm_raw);
+    const int kk = ka + kb, row = kk + 1;            // padded row of one element
+    const int ti_n = (ka + 3) / 4, tj_n = (kb + 3) / 4, ntile = ti_n * tj_n;
+    const int eg_n = 256 / ntile;                     // element classes (>= 1)
+    const int t = threadIdx.x;
+    const int tile = t % ntile, eg = t / ntile;
+    const bool active = eg < eg_n;
+    const int i0 = 4 * (tile / tj_n), j0 = 4 * (tile % tj_n);
+    double acc[4][4][2];
 #pragma unroll
-    for (int m = 0; m < GMAXP; ++m) { ar[m] = 0; ai[m] = 0; }
-    int64_t nchunks = (nc + GCH - 1) / GCH;
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-        int64_t e0 = ch * GCH;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+    const int64_t nch = (nc + GE - 1) / GE;
+    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int64_t e0 = ch * GE;
         __syncthreads();
-        for (int t = threadIdx.x; t < (ka + kb) * GCH; t += blockDim.x) {
-            int v = t / GCH, e = t % GCH;
-            int64_t idx = e0 + e;
+        for (int q = t; q < kk * GE; q += 256) {
+            const int v = q / GE, e = q % GE;
+            const int64_t idx = e0 + e;
             double2 val = make_double2(0, 0);
-            if (idx < nc) val = v < ka ? A2[(int64_t)v * nc + idx] : B2[(int64_t)(v - ka) * nc + idx];
-            if (LOWP) gsf[t] = make_float2((float)val.x, (float)val.y);
-            else gsh[t] = val;
+            if (idx < nc) val = v < ka ? A[(int64_t)v * nc + idx] : B[(int64_t)(v - ka) * nc + idx];
+            V2 x;
+            x.x = (T)val.x;
+            x.y = (T)val.y;
+            sv[e * row + v] = x;
         }
         __syncthreads();
+        if (!active) continue;
+        T cr[4][4], ci[4][4];
 #pragma unroll
-        for (int m = 0; m < GMAXP; ++m) {
-            int q = threadIdx.x + 256 * m;
-            if (q < P) {
-                int i = q / kb, j = q % kb;
-                if (LOWP) {
-                    const float2 *x = gsf + i * GCH, *y = gsf + (ka + j) * GCH;
-                    float re = 0.f, im = 0.f;
-#pragma unroll 8
-                    for (int e = 0; e < GCH; ++e) {
-                        float2 u = x[e], w = y[e];
-                        re = fmaf(u.x, w.x, fmaf(u.y, w.y, re));
-                        im = fmaf(u.x, w.y, fmaf(-u.y, w.x, im));
-                    }
-                    ar[m] += re; ai[m] += im;
-                } else {
-                    const double2 *x = gsh + i * GCH, *y = gsh + (ka + j) * GCH;
-                    double re = ar[m], im = ai[m];
-#pragma unroll 8
-                    for (int e = 0; e < GCH; ++e) {
-                        double2 u = x[e], w = y[e];
-                        re = fma(u.x, w.x, fma(u.y, w.y, re));
-                        im = fma(u.x, w.y, fma(-u.y, w.x, im));
-                    }
-                    ar[m] = re; ai[m] = im;
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cr[a][b] = ci[a][b] = (T)0;
+        for (int e = eg; e < GE; e += eg_n) {
+            const V2 *r = sv + e * row;
+            V2 x[4], y[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) x[a] = (i0 + a < ka) ? r[i0 + a] : V2{(T)0, (T)0};
+#pragma unroll
+            for (int b = 0; b < 4; ++b) y[b] = (j0 + b < kb) ? r[ka + j0 + b] : V2{(T)0, (T)0};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {   // conj(x) y
+                    cr[a][b] = fma(x[a].x, y[b].x, fma(x[a].y, y[b].y, cr[a][b]));
+                    ci[a][b] = fma(x[a].x, y[b].y, fma(-x[a].y, y[b].x, ci[a][b]));
                 }
-            }
         }
-    }
 #pragma unroll
-    for (int m = 0; m < GMAXP; ++m) {
-        int q = threadIdx.x + 256 * m;
-        if (q < P) {
-            part[((int64_t)2 * q) * gridDim.x + blockIdx.x] = ar[m];
-            part[((int64_t)2 * q + 1) * gridDim.x + blockIdx.x] = ai[m];
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                acc[a][b][0] += (double)cr[a][b];
+                acc[a][b][1] += (double)ci[a][b];
+            }
+    }
+    // sum the element classes of each tile (fixed order), reusing the staging buffer
+    __syncthreads();
+    double *red = reinterpret_cast<double *>(gsm_raw);   // [ntile][32] partial of class 0 ...
+    for (int c = 0; c < eg_n; ++c) {
+        if (active && eg == c) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    double *d = red + tile * 32 + (a * 4 + b) * 2;
+                    if (c == 0) { d[0] = acc[a][b][0]; d[1] = acc[a][b][1]; }
+                    else { d[0] += acc[a][b][0]; d[1] += acc[a][b][1]; }
+                }
+        }
+        __syncthreads();
+    }
+    for (int q = t; q < ntile * 16; q += 256) {
+        const int tl = q / 16, ab = q % 16, a = ab / 4, b = ab % 4;
+        const int i = 4 * (tl / tj_n) + a, j = 4 * (tl % tj_n) + b;
+        if (i < ka && j < kb) {
+            const int pq = i * kb + j;
+            part[((int64_t)2 * pq) * gridDim.x + blockIdx.x] = red[tl * 32 + ab * 2];
+            part[((int64_t)2 * pq + 1) * gridDim.x + blockIdx.x] = red[tl * 32 + ab * 2 + 1];
         }
     }
 }
 
-// LOWP: the k-term sums in FP32 (inputs rounded to FP32), stored as FP64
+// V_j = sum_i W_i C[i][j] (j < kc): each thread computes RE elements for a block of
+// up to RJ output vectors, the coefficients read from shared memory (the same word for
+// all threads of a warp); each W value it loads feeds RJ multiply-adds.  LOWP: values and
+// coefficients rounded to FP32, the sums in FP32.
+#define RJ 16
+#define RE 2
 template <bool LOWP>
-__global__ void rotate_kernel(const double *__restrict__ W, int ka, const double2 *__restrict__ C, int kc,
-                              int64_t nc, double *__restrict__ V)
+__global__ void __launch_bounds__(256) rotate_tile_kernel(const double2 *__restrict__ W, int ka,
+                                                          const double2 *__restrict__ C, int kc, int64_t nc,
+                                                          double2 *__restrict__ V)
 {
-    extern __shared__ double2 csh[];
-    float2 *csf = reinterpret_cast<float2 *>(csh);
-    for (int t = threadIdx.x; t < ka * kc; t += blockDim.x) {
-        if (LOWP) csf[t] = make_float2((float)C[t].x, (float)C[t].y);
-        else csh[t] = C[t];
+    typedef typename std::conditional<LOWP, float2, double2>::type V2;
+    typedef typename std::conditional<LOWP, float, double>::type T;
+    extern __shared__ __align__(16) unsigned char rsm_raw[];
+    V2 *cs = reinterpret_cast<V2 *>(rsm_raw);         // [ka][kc]
+    for (int q = threadIdx.x; q < ka * kc; q += blockDim.x) {
+        V2 x;
+        x.x = (T)C[q].x;
+        x.y = (T)C[q].y;
+        cs[q] = x;
     }
     __syncthreads();
-    const double2 *W2 = reinterpret_cast<const double2 *>(W);
-    double2 *V2 = reinterpret_cast<double2 *>(V);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
-        for (int j0 = 0; j0 < kc; j0 += 8) {
-            typedef typename std::conditional<LOWP, float, double>::type T;
-            T re[8], im[8];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * RE;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * RE + threadIdx.x; base < nc; base += stride) {
+        for (int j0 = 0; j0 < kc; j0 += RJ) {
+            T ar[RE][RJ], ai[RE][RJ];
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) { re[jj] = 0; im[jj] = 0; }
+            for (int u = 0; u < RE; ++u)
+#pragma unroll
+                for (int jj = 0; jj < RJ; ++jj) ar[u][jj] = ai[u][jj] = (T)0;
             for (int i = 0; i < ka; ++i) {
-                double2 w = W2[(int64_t)i * nc + e];
-                T wx = (T)w.x, wy = (T)w.y;
+                T wr[RE], wi[RE];
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
+                for (int u = 0; u < RE; ++u) {
+                    const int64_t e = base + (int64_t)u * blockDim.x;
+                    double2 w = e < nc ? __ldg(W + (int64_t)i * nc + e) : make_double2(0, 0);
+                    wr[u] = (T)w.x;
+                    wi[u] = (T)w.y;
+                }
+                const V2 *crow = cs + i * kc + j0;
+#pragma unroll
+                for (int jj = 0; jj < RJ; ++jj) {
                     if (j0 + jj < kc) {
-                        T cx, cy;
-                        if (LOWP) { float2 c = csf[i * kc + j0 + jj]; cx = c.x; cy = c.y; }
-                        else { double2 c = csh[i * kc + j0 + jj]; cx = (T)c.x; cy = (T)c.y; }
-                        re[jj] = wx * cx - wy * cy + re[jj];
-                        im[jj] = wx * cy + wy * cx + im[jj];
+                        const V2 c = crow[jj];
+#pragma unroll
+                        for (int u = 0; u < RE; ++u) {
+                            ar[u][jj] = fma(wr[u], c.x, fma(-wi[u], c.y, ar[u][jj]));
+                            ai[u][jj] = fma(wr[u], c.y, fma(wi[u], c.x, ai[u][jj]));
+                        }
                     }
                 }
             }
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-                if (j0 + jj < kc) V2[(int64_t)(j0 + jj) * nc + e] = make_double2((double)re[jj], (double)im[jj]);
+            for (int jj = 0; jj < RJ; ++jj)
+                if (j0 + jj < kc)
+#pragma unroll
+                    for (int u = 0; u < RE; ++u) {
+                        const int64_t e = base + (int64_t)u * blockDim.x;
+                        if (e < nc) V[(int64_t)(j0 + jj) * nc + e] = make_double2((double)ar[u][jj], (double)ai[u][jj]);
+                    }
         }
     }
 }
@@ -397,19 +448,21 @@ cudaError_t qs_resid2(const double *a, const double *b, const double *theta, int
 cudaError_t qs_gram(const double *A, int ka, const double *B, int kb, int64_t nr, double *part,
                     double2 *G, cudaStream_t st, int lowp)
 {
-    if (ka * kb > 256 * GMAXP) return cudaErrorInvalidValue;
+    if (ka < 1 || kb < 1 || ka > 64 || kb > 64) return cudaErrorInvalidValue;
     int64_t nc = nr / 2;
-    size_t sm = (size_t)(ka + kb) * GCH * sizeof(double2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(gram_part<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * GCH * 16);
-        cudaFuncSetAttribute(gram_part<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * GCH * 16);
-        attr = true;
-    }
-    int64_t nch = (nc + GCH - 1) / GCH;
+    const int row = ka + kb + 1;
+    const size_t stage = (size_t)GE * row * (lowp ? sizeof(float2) : sizeof(double2));
+    const size_t red = (size_t)((ka + 3) / 4) * ((kb + 3) / 4) * 32 * sizeof(double);
+    const size_t sm = stage > red ? stage : red;
+    static std::once_flag attr;
+    std::call_once(attr, [] {
+        cudaFuncSetAttribute(gram_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(gram_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    });
+    int64_t nch = (nc + GE - 1) / GE;
     int nb = (int)(nch < QS_RED_BLOCKS ? nch : QS_RED_BLOCKS);
-    if (lowp) gram_part<true><<<nb, 256, sm, st>>>(A, ka, B, kb, nc, part);
-    else gram_part<false><<<nb, 256, sm, st>>>(A, ka, B, kb, nc, part);
+    if (lowp) gram_tile_kernel<true><<<nb, 256, sm, st>>>((const double2 *)A, ka, (const double2 *)B, kb, nc, part);
+    else gram_tile_kernel<false><<<nb, 256, sm, st>>>((const double2 *)A, ka, (const double2 *)B, kb, nc, part);
     finalize_sum<<<2 * ka * kb, 256, 0, st>>>(part, nb, 1, reinterpret_cast<double *>(G));
     qs_note_launches(2);
     return cudaGetLastError();
@@ -418,16 +471,18 @@ cudaError_t qs_gram(const double *A, int ka, const double *B, int kb, int64_t nr
 cudaError_t qs_rotate(const double *W, int ka, const double2 *C, int kc, int64_t nr, double *V, cudaStream_t st,
                       int lowp)
 {
+    if (ka < 1 || kc < 1 || ka > 64 || kc > 64) return cudaErrorInvalidValue;
     int64_t nc = nr / 2;
-    size_t sm = (size_t)ka * kc * sizeof(double2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(rotate_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
-        cudaFuncSetAttribute(rotate_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
-        attr = true;
-    }
-    if (lowp) rotate_kernel<true><<<grid_for(nc, 256), 256, sm, st>>>(W, ka, C, kc, nc, V);
-    else rotate_kernel<false><<<grid_for(nc, 256), 256, sm, st>>>(W, ka, C, kc, nc, V);
+    size_t sm = (size_t)ka * kc * (lowp ? sizeof(float2) : sizeof(double2));
+    static std::once_flag attr;
+    std::call_once(attr, [] {
+        cudaFuncSetAttribute(rotate_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
+        cudaFuncSetAttribute(rotate_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * 16);
+    });
+    int64_t blocks = (nc + 256 * RE - 1) / (256 * RE);
+    int nb = (int)(blocks < 4 * 152 ? blocks : 4 * 152);
+    if (lowp) rotate_tile_kernel<true><<<nb, 256, sm, st>>>((const double2 *)W, ka, C, kc, nc, (double2 *)V);
+    else rotate_tile_kernel<false><<<nb, 256, sm, st>>>((const double2 *)W, ka, C, kc, nc, (double2 *)V);
     qs_note_launches(1);
     return cudaGetLastError();
 }

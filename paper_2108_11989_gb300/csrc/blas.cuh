@@ -43,6 +43,8 @@ cudaError_t qs_fill_gauss(double *x, int64_t n, uint64_t seed, cudaStream_t st);
 cudaError_t qs_scaled_copy(double *x, const double *b, const double *coef, int k, int64_t nr, cudaStream_t st);
 // out[r] = 1 / sqrt(in[r]) (0 stays 0), or theta^-2 style maps, on device
 cudaError_t qs_map_scalars(const double *in, double *out, int k, int mode, cudaStream_t st);
+// C* partner map P v = C T gamma_5 v^* of k FP64 vectors (partner.cu); in != out
+cudaError_t qs_partner(const double *in, double *out, const Geom &g, int k, int tiled, cudaStream_t st);
 // single-CTA dense kernels (k <= 64)
 cudaError_t qs_chol_rinv(const double2 *G, int k, double2 *Rinv, int *info, cudaStream_t st);
 cudaError_t qs_herm_eig(const double2 *H, int k, double *evals, double2 *Y, int *info, cudaStream_t st);

@@ -16,6 +16,7 @@ struct ProfState {
         cudaEvent_t a, b;
         int prec;
         double bytes;
+        int launches;
     };
     std::vector<Rec> pending;
     std::vector<cudaEvent_t> pool;
@@ -44,7 +45,7 @@ static int prof_resolve(qs_lattice *lat)
         float ms = 0.f;
         QS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
         qs_kernel_prof &k = p->acc.dslash[r.prec];
-        k.launches += 1;
+        k.launches += r.launches;
         k.ms += ms;
         k.bytes += r.bytes;
         p->pool.push_back(r.a);
@@ -90,7 +91,7 @@ extern "C" int qs_get_profile(qs_lattice *lat, qs_profile *prof)
     return QS_OK;
 }
 
-static char g_last_cuda_error[256] = "";
+static thread_local char g_last_cuda_error[256] = "";
 static long long g_launches = 0;
 
 void qs_note_launches(int n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
@@ -290,7 +291,17 @@ static int prof_end(qs_lattice *lat, cudaEvent_t ea, cudaEvent_t eb, int prec, d
 {
     if (!ea) return QS_OK;
     QS_CUDA(cudaEventRecord(eb, lat->stream));
-    lat->prof->pending.push_back({ea, eb, prec, bytes});
+    lat->prof->pending.push_back({ea, eb, prec, bytes, 1});
+    return QS_OK;
+}
+
+int qs_prof_begin(qs_lattice *lat, cudaEvent_t *ea, cudaEvent_t *eb) { return prof_begin(lat, ea, eb); }
+
+int qs_prof_end(qs_lattice *lat, cudaEvent_t ea, cudaEvent_t eb, int prec, double bytes, int launches)
+{
+    if (!ea) return QS_OK;
+    QS_CUDA(cudaEventRecord(eb, lat->stream));
+    lat->prof->pending.push_back({ea, eb, prec, bytes, launches});
     return QS_OK;
 }
 
@@ -331,9 +342,12 @@ static int prec_of_storage(int storage)
 }
 
 int qs_d32_run(qs_lattice *lat, int storage, const double *m0, const void *in, void *out, int nrhs, int gamma5,
-               const void *cheb_y, const void *cheb_x, double cheb_c, double cheb_s1, double cheb_s2)
+               const void *cheb_y, const void *cheb_x, double cheb_c, double cheb_s1, double cheb_s2,
+               const float *coef_dev, const float *dm_dev)
 {
     D32Call c;
+    c.coef_dev = coef_dev;
+    c.dm_dev = dm_dev;
     c.g = lat->g;
     c.links = lat->links32;
     c.clov = lat->clov32;
@@ -362,6 +376,7 @@ int qs_d32_run(qs_lattice *lat, int storage, const double *m0, const void *in, v
                 v = time_variants(lat, qs_d32_nvariants(), [&](int q) { return qs_d32_launch(c, q, lat->stream); }, &st);
                 if (st != QS_OK) return st;
                 tune_store(key, v);
+                if (getenv("QS_VERBOSE")) fprintf(stderr, "[qstar] autotune %s -> variant %d\n", key.c_str(), v);
             }
         }
         tv = v + 1;

@@ -64,7 +64,9 @@ struct D32Call {
     const void *y, *x;     // cheb = 1: out = s1 (Q in - c y) - s2 x
     int storage, nrhs, gamma5, cheb;
     double cheb_c, cheb_s1, cheb_s2;
-    const double *m0;      // host, nrhs masses
+    const double *m0;      // host, nrhs masses (ignored where dm_dev is set)
+    const float *coef_dev; // NULL, or device (c, s1, s2) of the Chebyshev epilogue
+    const float *dm_dev;   // NULL, or device 4 + m0 per right-hand side
 };
 int qs_d32_nvariants();
 int64_t qs_d32_vec_bytes(int storage, int64_t Ns);

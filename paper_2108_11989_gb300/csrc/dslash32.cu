@@ -28,6 +28,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 namespace {
 
 typedef float2 cf;
@@ -246,6 +248,9 @@ struct D32 {
     int nrhs, gamma5;
     float c, s1, s2;    // CHEB: out = s1 (Q in - c y) - s2 x
     float dm[QS_MAX_RHS];   // 4 + m0 per right-hand side
+    // device-side overrides (for launches replayed from a CUDA graph): if set, (c, s1, s2)
+    // are read from coef[0..2] and 4 + m0 of right-hand side r from dmdev[r]
+    const float *coef, *dmdev;
 };
 
 template <int MU, int STEP, class S, int G>
@@ -318,7 +323,7 @@ __device__ __forceinline__ void site_kernel(const D32 &a, unsigned bx, unsigned 
 #pragma unroll
                 for (int i = 0; i < 12; ++i) v[g][i] = make_float2(0.f, 0.f);
             }
-            const float dm = a.dm[g < nr ? r0 + g : r0];
+            const float dm = a.dmdev ? __ldg(a.dmdev + (g < nr ? r0 + g : r0)) : a.dm[g < nr ? r0 + g : r0];
 #pragma unroll
             for (int i = 0; i < 12; ++i) acc[g][i] = make_float2(dm * v[g][i].x, dm * v[g][i].y);
         }
@@ -357,10 +362,13 @@ __device__ __forceinline__ void site_kernel(const D32 &a, unsigned bx, unsigned 
                 cf yv[12], xv[12];
                 S::ld(a.y + off, s, yv);
                 S::ld(a.x + off, s, xv);
+                const float cc = a.coef ? __ldg(a.coef) : a.c;
+                const float s1 = a.coef ? __ldg(a.coef + 1) : a.s1;
+                const float s2 = a.coef ? __ldg(a.coef + 2) : a.s2;
 #pragma unroll
                 for (int i = 0; i < 12; ++i) {
-                    acc[g][i].x = a.s1 * fmaf(-a.c, yv[i].x, acc[g][i].x) - a.s2 * xv[i].x;
-                    acc[g][i].y = a.s1 * fmaf(-a.c, yv[i].y, acc[g][i].y) - a.s2 * xv[i].y;
+                    acc[g][i].x = s1 * fmaf(-cc, yv[i].x, acc[g][i].x) - s2 * xv[i].x;
+                    acc[g][i].y = s1 * fmaf(-cc, yv[i].y, acc[g][i].y) - s2 * xv[i].y;
                 }
             }
             S::st(a.out + off, s, acc[g]);
@@ -481,13 +489,15 @@ template <class S>
 cudaError_t batch_launch(const D32B &b, cudaStream_t st)
 {
     static int per_sm = 0, nsm = 0;
-    if (!per_sm) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dslash32_batch_kernel<S>, 128, 0);
         if (per_sm < 1) per_sm = 1;
-    }
+        if (nsm < 1) nsm = 1;
+    });
     const unsigned total = b.off[b.n];
     const unsigned grid = total < (unsigned)(per_sm * nsm) ? total : (unsigned)(per_sm * nsm);
     dslash32_batch_kernel<S><<<grid, 128, 0, st>>>(b);
@@ -516,6 +526,7 @@ cudaError_t qs_d32_batch_launch(const D32BatchItem *items, int n, int storage, i
         a.nrhs = it.nrhs;
         a.gamma5 = gamma5;
         a.c = a.s1 = a.s2 = 0.f;
+        a.coef = a.dmdev = nullptr;
         for (int r = 0; r < it.nrhs; ++r) a.dm[r] = (float)(4.0 + it.m0[r]);
         const unsigned spb = 128 / QS_B_RL;
         b.nbx[i] = (unsigned)((it.g.Ns + spb - 1) / spb);
@@ -560,7 +571,9 @@ cudaError_t qs_d32_launch(const D32Call &c, int variant, cudaStream_t st)
     a.c = (float)c.cheb_c;
     a.s1 = (float)c.cheb_s1;
     a.s2 = (float)c.cheb_s2;
-    for (int r = 0; r < c.nrhs; ++r) a.dm[r] = (float)(4.0 + c.m0[r]);
+    for (int r = 0; r < c.nrhs; ++r) a.dm[r] = c.m0 ? (float)(4.0 + c.m0[r]) : 0.f;
+    a.coef = c.coef_dev;
+    a.dmdev = c.dm_dev;
     const bool cheb = c.cheb;
     switch (c.storage) {
     case QS_D32_F32_TILED: return launch_storage<StF32Tiled>(variant, cheb, a, st);

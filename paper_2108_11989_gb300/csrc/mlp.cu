@@ -189,6 +189,8 @@ extern "C" int qs_mlp_destroy(qs_mlp *n)
 
 extern "C" int64_t qs_mlp_n_params(const qs_mlp *n) { return n ? (int64_t)n->np : 0; }
 
+cudaStream_t qs_mlp_stream(const qs_mlp *n) { return n->stream; }
+
 extern "C" int qs_mlp_set_params(qs_mlp *n, const float *host)
 {
     if (!n || !host) return QS_EINVAL;

@@ -158,4 +158,8 @@ int qs_dslash_run(qs_lattice *lat, int prec, const double *m0, const void *in, v
 // epilogue out = s1 (Q in - c y) - s2 x (cheb_y != NULL)
 int qs_d32_run(qs_lattice *lat, int storage, const double *m0, const void *in, void *out, int nrhs, int gamma5,
                const void *cheb_y = nullptr, const void *cheb_x = nullptr, double cheb_c = 0,
-               double cheb_s1 = 0, double cheb_s2 = 0);
+               double cheb_s1 = 0, double cheb_s2 = 0, const float *coef_dev = nullptr,
+               const float *dm_dev = nullptr);
+// record one profiling interval covering `launches` operator launches (graph replays)
+int qs_prof_begin(qs_lattice *lat, cudaEvent_t *ea, cudaEvent_t *eb);
+int qs_prof_end(qs_lattice *lat, cudaEvent_t ea, cudaEvent_t eb, int prec, double bytes, int launches);

@@ -30,6 +30,7 @@
 #include <time.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 
@@ -47,6 +48,8 @@ extern "C" void qs_sign_default_opts(qs_sign_opts *o)
     // moderate relative accuracy keeps every mass point cheap
     o->eig.tol = 1e-5;
 }
+
+cudaStream_t qs_mlp_stream(const qs_mlp *n);
 
 namespace {
 
@@ -147,12 +150,15 @@ int propose(Flow &f, double lb, double *dm)
     for (int j = 0; j < 8; ++j)
         for (int i = 0; i < QS_WINDOW; ++i)
             x[j * QS_WINDOW + i] = j < nh ? (float)(f.hist[nh - 1 - j].v[i] / lb) : 0.f;
-    cudaStream_t st = f.lat->stream;
+    // the network may run on another stream than the lattice: order the copies by
+    // synchronising each stream before the next one uses the data
+    cudaStream_t st = f.lat->stream, ns = qs_mlp_stream(f.o.step_model);
     QS_CUDA(cudaMemcpyAsync(f.dX, x, sizeof(x), cudaMemcpyHostToDevice, st));
-    QS_TRY(qs_mlp_forward(f.o.step_model, f.dX, 1, f.dY));
-    float y0 = 0.f;
-    QS_CUDA(cudaMemcpyAsync(&y0, f.dY, sizeof(float), cudaMemcpyDeviceToHost, st));
     QS_CUDA(cudaStreamSynchronize(st));
+    QS_TRY(qs_mlp_forward(f.o.step_model, f.dX, 1, f.dY));
+    QS_CUDA(cudaStreamSynchronize(ns));
+    float y0 = 0.f;
+    QS_CUDA(cudaMemcpy(&y0, f.dY, sizeof(float), cudaMemcpyDeviceToHost));
     double ly = std::min(std::max((double)y0, log(f.o.c)), log(8.0));
     *dm = lb * exp(ly);
     return QS_OK;
@@ -165,6 +171,7 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
 {
     if (!lat || !sign) return QS_EINVAL;
     if (!lat->gauge_loaded) return QS_EINVAL;
+    QS_CUDA(cudaSetDevice(lat->device));
     qs_sign_report local;
     qs_sign_report *rep = report ? report : &local;
     memset(rep, 0, sizeof(*rep));
@@ -360,4 +367,29 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
     }
     rep->fail_reason = 5;
     return finish(QS_ENOCONV);
+}
+
+// The batched form: the flows of several configurations are independent (Sec. 3: the
+// algorithm is run on each configuration), each with its own sequence of masses, so they
+// run concurrently -- one host thread per configuration, each on its handle's stream --
+// and the GPU executes their kernels side by side.
+extern "C" int qs_pfaffian_sign_batch(qs_lattice *const *lats, int n, const double *m0_targets,
+                                      const qs_sign_opts *opts, int *signs, int *status, qs_sign_report *reports)
+{
+    if (!lats || n < 1 || !m0_targets || !signs || !status) return QS_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!lats[i] || !lats[i]->gauge_loaded) return QS_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (lats[j] == lats[i]) return QS_EINVAL;   // a handle serves one flow at a time
+    }
+    std::vector<std::thread> th;
+    th.reserve(n);
+    for (int i = 0; i < n; ++i)
+        th.emplace_back([=] {
+            status[i] = qs_pfaffian_sign(lats[i], m0_targets[i], opts, &signs[i], reports ? &reports[i] : nullptr);
+        });
+    for (auto &t : th) t.join();
+    for (int i = 0; i < n; ++i)
+        if (status[i] != QS_OK) return status[i];
+    return QS_OK;
 }

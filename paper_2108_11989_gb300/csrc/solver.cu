@@ -19,7 +19,21 @@
 #include <algorithm>
 #include <vector>
 
+// A captured Chebyshev filter (2 d operator launches on fixed buffers, coefficients
+// and masses read from device tables), replayed with cudaGraphLaunch.
+struct FilterGraph {
+    int kf, d, storage;
+    const void *links, *clov;   // the gauge field the launches were captured with
+    cudaGraphExec_t exec;
+    void *res;                  // the buffer holding the filtered block after a replay
+};
+#define QS_GRAPH_MAX_DEG 511
+#define QS_NGRAPH 6
+
 struct Workspace {
+    FilterGraph fg[QS_NGRAPH];
+    int nfg;
+    float *coef_dev, *coef_host;   // [3 * QS_GRAPH_MAX_DEG + 64]: (c, s1, s2) per step, then 4 + m0
     int k;
     int64_t nr;
     double *blk64[6];     // FP64 blocks [k][nr]
@@ -31,16 +45,20 @@ struct Workspace {
     double *hp;           // pinned host mirror of ds (S_NSLOT x 64)
     int *hi;              // pinned host ints (64 + 8)
     int have_V;
+    int pinv;             // the span of blk64[0] is closed under the C* partner map
     int64_t f32_count, f64_count, cg_count;
 };
 
 #define DS(ws, slot) ((ws)->ds + 64 * (slot))
 enum { S_TMP = 0, S_THETA = 1, S_COEF = 2, S_RR = 3, S_RR0 = 4, S_PAP = 5, S_BETA = 6, S_ONES = 7, S_RN = 8,
-       S_NSLOT = 12 };
+       S_DOT = 9 /* two slots */, S_VN = 11, S_NSLOT = 12 };
 
 static void ws_free(Workspace *w)
 {
     if (!w) return;
+    for (int i = 0; i < w->nfg; ++i) cudaGraphExecDestroy(w->fg[i].exec);
+    cudaFree(w->coef_dev);
+    cudaFreeHost(w->coef_host);
     for (int i = 0; i < 6; ++i) cudaFree(w->blk64[i]);
     for (int i = 0; i < 5; ++i) cudaFree(w->blk32[i]);
     cudaFree(w->part); cudaFree(w->G); cudaFree(w->Rinv); cudaFree(w->Hm); cudaFree(w->Ym);
@@ -80,6 +98,8 @@ static int ws_alloc(qs_lattice *lat, Workspace *w, int k)
     CK(cudaMalloc(&w->di, 72 * sizeof(int)));
     CK(cudaMallocHost(&w->hp, S_NSLOT * 64 * sizeof(double)));
     CK(cudaMallocHost(&w->hi, 72 * sizeof(int)));
+    CK(cudaMalloc(&w->coef_dev, (3 * QS_GRAPH_MAX_DEG + 64) * sizeof(float)));
+    CK(cudaMallocHost(&w->coef_host, (3 * QS_GRAPH_MAX_DEG + 64) * sizeof(float)));
     CK(cudaMemsetAsync(w->di, 0, 72 * sizeof(int), lat->stream));
     for (int i = 0; i < 64; ++i) w->hp[i] = 1.0;
     CK(cudaMemcpyAsync(DS(w, S_ONES), w->hp, 64 * sizeof(double), cudaMemcpyHostToDevice, lat->stream));
@@ -130,9 +150,12 @@ static int sync_read(qs_lattice *lat, Workspace *w, int slot, int n)
 }
 
 // column scaling + Cholesky-QR twice: X becomes orthonormal (tmp is clobbered)
-// lowp: FP32 Gram and rotation (filter stage, where the block is far from
-// converged and FP32 rounding is far below its residuals)
-static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp, int k, int lowp)
+// glow: FP32 products in the Gram matrices; rlow: FP32 products in the rotations (the
+// filter stage, where the block is far from converged and FP32 rounding is far below
+// its residuals).  Rounding in a rotation perturbs the vectors themselves (by ~1e-7,
+// an absolute residual floor of ~1e-7 ||Q||), rounding in a Gram matrix only the
+// coefficients of the next rotation.
+static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp, int k, int glow, int rlow)
 {
     cudaStream_t st = lat->stream;
     CK(qs_norm2<double>(X, k, w->nr, w->part, DS(w, S_TMP), st));
@@ -140,9 +163,9 @@ static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp,
     CK(qs_scale_cols(X, DS(w, S_COEF), k, w->nr, st));
     for (int pass = 0; pass < 2; ++pass) {
         double *src = pass == 0 ? X : tmp, *dst = pass == 0 ? tmp : X;
-        CK(qs_gram(src, k, src, k, w->nr, w->part, w->G, st, lowp));
+        CK(qs_gram(src, k, src, k, w->nr, w->part, w->G, st, glow));
         CK(qs_chol_rinv(w->G, k, w->Rinv, w->di + 64 + pass, st));
-        CK(qs_rotate(src, k, w->Rinv, k, w->nr, dst, st, lowp));
+        CK(qs_rotate(src, k, w->Rinv, k, w->nr, dst, st, rlow));
     }
     return QS_OK;
 }
@@ -157,7 +180,11 @@ static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp,
 // large r).  The pairs are therefore ordered by <v, Q^2 v> = theta^2 + r^2, which is
 // close to lambda^2 for a genuine pair and large for a spurious one.
 // prec: operator precision (FP32 while far from convergence, FP64 otherwise).
-static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *rz, int prec)
+// glow: FP32 products in the Gram matrices (then the block is orthonormal only to ~1e-7
+// and every residual is divided by ||v||); the rotations use FP32 products only with
+// the FP32 operator.  Some eigenvalue of Q lies within ||Q v - theta v|| / ||v|| of
+// theta for any theta and v, so the returned bounds hold whatever the rounding of H.
+static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *rz, int prec, int glow)
 {
     cudaStream_t st = lat->stream;
     if (prec == QS_F64) {
@@ -167,19 +194,29 @@ static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *
         QS_TRY(opQ(lat, w, QS_F32, m0, w->blk32[0], w->blk32[1], k));
         CK(qs_f2d(w->blk32[1], w->blk64[1], k, w->nr, st));
     }
-    const int lowp = prec == QS_F32;
-    CK(qs_gram(w->blk64[1], k, w->blk64[1], k, w->nr, w->part, w->Hm, st, lowp));
+    const int rlow = prec == QS_F32;
+    glow = glow || rlow;
+    // the Q^2 Ritz values only place the filter interval: FP32 products always
+    CK(qs_gram(w->blk64[1], k, w->blk64[1], k, w->nr, w->part, w->Hm, st, 1));
     CK(qs_herm_eig(w->Hm, k, DS(w, S_RN), w->Ym, w->di + 66, st));
-    CK(qs_gram(w->blk64[0], k, w->blk64[1], k, w->nr, w->part, w->Hm, st, lowp));
+    CK(qs_gram(w->blk64[0], k, w->blk64[1], k, w->nr, w->part, w->Hm, st, glow));
     CK(qs_herm_eig(w->Hm, k, DS(w, S_THETA), w->Ym, w->di + 67, st));
-    CK(qs_rotate(w->blk64[0], k, w->Ym, k, w->nr, w->blk64[2], st, lowp));
-    CK(qs_rotate(w->blk64[1], k, w->Ym, k, w->nr, w->blk64[3], st, lowp));
+    CK(qs_rotate(w->blk64[0], k, w->Ym, k, w->nr, w->blk64[2], st, rlow));
+    CK(qs_rotate(w->blk64[1], k, w->Ym, k, w->nr, w->blk64[3], st, rlow));
     std::swap(w->blk64[0], w->blk64[2]);
     std::swap(w->blk64[1], w->blk64[3]);
+    const bool scale = glow && prec == QS_F64;
+    if (scale) CK(qs_norm2<double>(w->blk64[0], k, w->nr, w->part, DS(w, S_VN), st));
     CK(qs_resid2(w->blk64[1], w->blk64[0], DS(w, S_THETA), k, w->nr, w->part, DS(w, S_TMP), st));
     CK(cudaMemcpyAsync(w->hp + 64 * S_THETA, DS(w, S_THETA), k * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(w->hp + 64 * S_RN, DS(w, S_RN), k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (scale) CK(cudaMemcpyAsync(w->hp + 64 * S_VN, DS(w, S_VN), k * sizeof(double), cudaMemcpyDeviceToHost, st));
     QS_TRY(sync_read(lat, w, S_TMP, k));
+    if (scale)
+        for (int i = 0; i < k; ++i) {
+            const double vn = w->hp[64 * S_VN + i];
+            w->hp[64 * S_TMP + i] = vn > 0 ? w->hp[64 * S_TMP + i] / vn : INFINITY;
+        }
     if (w->hi[64] || w->hi[65]) return QS_ENUMERIC;   // Cholesky-QR broke down
     if (w->hi[66] || w->hi[67]) return QS_ENOCONV;    // Jacobi hit its sweep cap
     double th[64], rs[64], key[64];
@@ -208,27 +245,109 @@ static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *
 // O(1)).  Each degree is two operator launches: T = Q Y, then the second one computes
 // Y_new = s1 (Q T - c Y) - s2 Y_old in its epilogue.  storage: QS_D32_F32_TILED, or a
 // 16-bit storage whose vectors (52 B per site) live in the same FP32 blocks.
+// the launches of one filter, in order: step i (0-based) is T = Q Y_i, then
+// Y_{i+1} = s1_i (Q T - c Y_i) - s2_i Y_{i-1}; returns the result buffer.  With coef_dev the
+// coefficients of step i and the masses are read from the device tables.
+static int cheb_launches(qs_lattice *lat, Workspace *w, const double *m, int k, int d, int storage,
+                         const double *cf, const float *coef_dev, const float *dm_dev, void **res)
+{
+    void *X = w->blk32[0], *Y = w->blk32[1], *Yn = w->blk32[2], *T = w->blk32[3];
+    for (int i = 0; i < d; ++i) {
+        void *in = i == 0 ? X : Y, *yv = i == 0 ? X : Y, *xv = X, *out = i == 0 ? Y : Yn;
+        QS_TRY(qs_d32_run(lat, storage, m, in, T, k, 1, nullptr, nullptr, 0, 0, 0, nullptr, dm_dev));
+        QS_TRY(qs_d32_run(lat, storage, m, T, out, k, 1, yv, xv, cf[3 * i], cf[3 * i + 1], cf[3 * i + 2],
+                          coef_dev ? coef_dev + 3 * i : nullptr, dm_dev));
+        if (i > 0) {
+            void *tmp = X; X = Y; Y = Yn; Yn = tmp;
+        }
+    }
+    *res = Y;
+    return QS_OK;
+}
+
+static bool use_graphs()
+{
+    static const bool on = [] {
+        const char *e = getenv("QS_NO_GRAPHS");
+        return !(e && atoi(e));
+    }();
+    return on;
+}
+
+// Chebyshev filter of degree d on Q^2 over [a, b] with FP32 arithmetic: blk32[0] (in)
+// -> result in *res (one of blk32), scaled three-term recurrence (values at 0 kept
+// O(1)).  Each degree is two operator launches: T = Q Y, then the second one computes
+// Y_new = s1 (Q T - c Y) - s2 Y_old in its epilogue.  storage: QS_D32_F32_TILED, or a
+// 16-bit storage whose vectors (52 B per site) live in the same FP32 blocks.  On a
+// handle with its own stream the 2 d launches are captured once per (k, d, storage) as
+// a CUDA graph and replayed; only the coefficient table changes between replays.
 static int cheb_filter(qs_lattice *lat, Workspace *w, double m0, int k, int d, double a, double b, int storage,
                        void **res)
 {
-    void *X = w->blk32[0], *Y = w->blk32[1], *Yn = w->blk32[2], *T = w->blk32[3];
+    cudaStream_t st = lat->stream;
     double m[QS_MAX_RHS];
     for (int r = 0; r < k; ++r) m[r] = m0;
     double e = 0.5 * (b - a), c = 0.5 * (b + a);
     double sigma1 = e / (0.0 - c);
     double sigma = sigma1, g = 2.0 / sigma1;
-    QS_TRY(qs_d32_run(lat, storage, m, X, T, k, 1));
-    QS_TRY(qs_d32_run(lat, storage, m, T, Y, k, 1, X, X, c, sigma1 / e, 0.0));
-    w->f32_count += 2 * k;
-    for (int i = 2; i <= d; ++i) {
+    std::vector<double> cf(3 * (size_t)d);
+    cf[0] = c; cf[1] = sigma1 / e; cf[2] = 0.0;
+    for (int i = 1; i < d; ++i) {
         double s2 = 1.0 / (g - sigma);
-        QS_TRY(qs_d32_run(lat, storage, m, Y, T, k, 1));
-        QS_TRY(qs_d32_run(lat, storage, m, T, Yn, k, 1, Y, X, c, 2.0 * s2 / e, sigma * s2));
-        w->f32_count += 2 * k;
-        void *tmp = X; X = Y; Y = Yn; Yn = tmp;
+        cf[3 * i] = c;
+        cf[3 * i + 1] = 2.0 * s2 / e;
+        cf[3 * i + 2] = sigma * s2;
         sigma = s2;
     }
-    *res = Y;
+    w->f32_count += 2 * (int64_t)k * d;
+    const bool tuned = lat->tuned32[storage][0][k] && lat->tuned32[storage][1][k];
+    if (!(use_graphs() && st != nullptr && d <= QS_GRAPH_MAX_DEG && tuned))
+        return cheb_launches(lat, w, m, k, d, storage, cf.data(), nullptr, nullptr, res);
+    FilterGraph *fgp = nullptr;
+    for (int i = 0; i < w->nfg; ++i) {
+        FilterGraph &f = w->fg[i];
+        if (f.kf == k && f.d == d && f.storage == storage && f.links == lat->links32 && f.clov == lat->clov32)
+            fgp = &f;
+    }
+    if (!fgp) {
+        if (w->nfg == QS_NGRAPH) {   // drop the oldest
+            cudaGraphExecDestroy(w->fg[0].exec);
+            memmove(&w->fg[0], &w->fg[1], (QS_NGRAPH - 1) * sizeof(FilterGraph));
+            --w->nfg;
+        }
+        FilterGraph f;
+        f.kf = k; f.d = d; f.storage = storage;
+        f.links = lat->links32; f.clov = lat->clov32;
+        const int64_t n0 = qs_kernel_launches();
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int s = cheb_launches(lat, w, m, k, d, storage, cf.data(), w->coef_dev, w->coef_dev + 3 * QS_GRAPH_MAX_DEG,
+                              &f.res);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e1 = cudaStreamEndCapture(st, &graph);
+        qs_note_launches((int)(n0 - qs_kernel_launches()));   // counted at replay instead
+        if (s != QS_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+        CK(e1);
+        cudaError_t e2 = cudaGraphInstantiate(&f.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e2);
+        w->fg[w->nfg++] = f;
+        fgp = &w->fg[w->nfg - 1];
+    }
+    float *hc = w->coef_host;
+    for (int i = 0; i < 3 * d; ++i) hc[i] = (float)cf[i];
+    for (int r = 0; r < k; ++r) hc[3 * QS_GRAPH_MAX_DEG + r] = (float)(4.0 + m0);
+    CK(cudaMemcpyAsync(w->coef_dev, hc, 3 * (size_t)d * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(w->coef_dev + 3 * QS_GRAPH_MAX_DEG, hc + 3 * QS_GRAPH_MAX_DEG, k * sizeof(float),
+                       cudaMemcpyHostToDevice, st));
+    cudaEvent_t ea, eb;
+    QS_TRY(qs_prof_begin(lat, &ea, &eb));
+    CK(cudaGraphLaunch(fgp->exec, st));
+    qs_note_launches(2 * d);
+    const double vs = (double)qs_d32_vec_bytes(storage, 1);
+    const double bytes = (double)lat->g.Ns * d * (vs * 6 * k + 2 * 72.0 * 4);
+    const int prec = storage == QS_D32_F16 ? QS_F16 : storage == QS_D32_BF16 ? QS_BF16 : QS_F32;
+    QS_TRY(qs_prof_end(lat, ea, eb, prec, bytes, 2 * d));
+    *res = fgp->res;
     return QS_OK;
 }
 
@@ -290,11 +409,10 @@ static int cg_f32(qs_lattice *lat, Workspace *w, double m0, int k, float *x, flo
 
 static int verbose()
 {
-    static int v = -1;
-    if (v < 0) {
+    static const int v = [] {
         const char *e = getenv("QS_VERBOSE");
-        v = e ? atoi(e) : 0;
-    }
+        return e ? atoi(e) : 0;
+    }();
     return v;
 }
 
@@ -326,6 +444,87 @@ static int solve_q2_mixed(qs_lattice *lat, Workspace *w, double m0, int k, const
     return QS_ENOCONV;
 }
 
+// k / 2 representatives of the block V = blk64[0] (device columns, written to sel)
+// whose span together with their C* partners P v is the span of V.  Candidates are
+// taken in Ritz order (rz->col).  If the span is known to be closed under P, M = V^H P V
+// (FP32 products) gives the coordinates of every partner, and a candidate is kept only
+// if it has a component of norm^2 > 1/2 outside span{v_s, P v_s} of those kept so far
+// (Gram-Schmidt in the k coordinates), so nearly degenerate pairs cannot both be picked.
+static int pick_representatives(qs_lattice *lat, Workspace *w, const Ritz *rz, int k, int *sel)
+{
+    const int h = k / 2;
+    if (!w->pinv) {
+        for (int i = 0; i < h; ++i) sel[i] = rz->col[i];
+        return QS_OK;
+    }
+    cudaStream_t st = lat->stream;
+    CK(qs_partner(w->blk64[0], w->blk64[3], lat->g, k, 1, st));
+    CK(qs_gram(w->blk64[0], k, w->blk64[3], k, w->nr, w->part, w->G, st, 1));
+    static thread_local double2 M[64 * 64];
+    CK(cudaMemcpyAsync(M, w->G, (size_t)k * k * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<std::vector<double2>> basis;
+    auto residual = [&](std::vector<double2> x) {
+        for (const auto &b : basis) {
+            double cr = 0, ci = 0;   // <b, x>
+            for (int j = 0; j < k; ++j) {
+                cr += b[j].x * x[j].x + b[j].y * x[j].y;
+                ci += b[j].x * x[j].y - b[j].y * x[j].x;
+            }
+            for (int j = 0; j < k; ++j) {
+                x[j].x -= cr * b[j].x - ci * b[j].y;
+                x[j].y -= cr * b[j].y + ci * b[j].x;
+            }
+        }
+        return x;
+    };
+    auto norm2 = [&](const std::vector<double2> &x) {
+        double n = 0;
+        for (int j = 0; j < k; ++j) n += x[j].x * x[j].x + x[j].y * x[j].y;
+        return n;
+    };
+    int n = 0;
+    bool used[64] = {false};
+    for (int i = 0; i < k && n < h; ++i) {
+        const int c = rz->col[i];
+        std::vector<double2> e(k, make_double2(0, 0));
+        e[c] = make_double2(1, 0);
+        std::vector<double2> r = residual(e);
+        double nr2 = norm2(r);
+        if (nr2 <= 0.5) continue;
+        sel[n++] = c;
+        used[c] = true;
+        for (int j = 0; j < k; ++j) { r[j].x /= sqrt(nr2); r[j].y /= sqrt(nr2); }
+        basis.push_back(r);
+        std::vector<double2> m(k);
+        for (int j = 0; j < k; ++j) m[j] = M[j * k + c];   // P v_c = sum_j v_j M[j][c]
+        std::vector<double2> rm = residual(m);
+        double nm2 = norm2(rm);
+        if (nm2 > 1e-6) {
+            for (int j = 0; j < k; ++j) { rm[j].x /= sqrt(nm2); rm[j].y /= sqrt(nm2); }
+            basis.push_back(rm);
+        }
+    }
+    for (int i = 0; i < k && n < h; ++i)   // not expected for a closed span
+        if (!used[rz->col[i]]) { sel[n++] = rz->col[i]; used[rz->col[i]] = true; }
+    return QS_OK;
+}
+
+// blk64[dst][0..h) = blk64[0][sel[i]] (scaled by coef[sel[i]] if coef != NULL)
+static int gather_columns(qs_lattice *lat, Workspace *w, const int *sel, int h, double *dst, const double *coef)
+{
+    for (int i = 0; i < h; ++i)
+        CK(cudaMemcpyAsync(dst + (size_t)i * w->nr, w->blk64[0] + (size_t)sel[i] * w->nr, w->nr * sizeof(double),
+                           cudaMemcpyDeviceToDevice, lat->stream));
+    if (coef) {
+        double c[64];
+        for (int i = 0; i < h; ++i) c[i] = coef[sel[i]];
+        CK(cudaMemcpyAsync(DS(w, S_COEF), c, h * sizeof(double), cudaMemcpyHostToDevice, lat->stream));
+        CK(qs_scale_cols(dst, DS(w, S_COEF), h, w->nr, lat->stream));
+    }
+    return QS_OK;
+}
+
 static double now_s()
 {
     struct timespec ts;
@@ -344,6 +543,7 @@ extern "C" void qs_eig_default_opts(qs_eig_opts *o)
     o->warm_start = 1;
     o->seed = 1;
     o->precision = QS_F32;
+    o->pairing = 1;
 }
 
 
@@ -357,11 +557,17 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
     int64_t f32_0 = w->f32_count, f64_0 = w->f64_count, cg_0 = w->cg_count;
     if (!(o->warm_start && w->have_V)) {
         CK(qs_fill_gauss(w->blk64[0], (int64_t)k * w->nr, o->seed * 0x9E3779B97F4A7C15ULL + 17, st));
+        w->pinv = 0;
     }
     w->have_V = 0;
     const bool plain = o->precision == QS_F64;
-    QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : 1));
-    QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, plain ? QS_F64 : QS_F32));
+    const bool pair = !plain && o->pairing && k >= 4;
+    // Gram products in FP32 also in the FP64-operator stages when the requested accuracy
+    // allows it (with the FP64 operator their rounding is ~1e-7 relative to the
+    // eigenvalue scale); rotations stay FP64 there
+    const int glow = (!plain && o->tol >= 1e-6) ? 1 : 0;
+    QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : 1, plain ? 0 : 1));
+    QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, plain ? QS_F64 : QS_F32, plain ? 0 : 1));
     // b >= lambda_max(Q^2): ||Q|| = ||D|| <= max_x ||4 + m0 + A(x)|| + ||hopping||,
     // ||hopping|| <= 4 (each direction is a partial isometry pair of norm 1)
     double qn = fabs(4.0 + m0) + lat->clov_norm + 4.0;
@@ -402,8 +608,9 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             std::swap(w->blk64[0], w->blk64[2]);
             CK(qs_fill_gauss(w->blk64[0] + (size_t)nconv * w->nr, (int64_t)(k - nconv) * w->nr,
                              o->seed * 0x2545F4914F6CDD1DULL + 977 * (restarts + 1), st));
-            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : 1));
-            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, plain ? QS_F64 : QS_F32));
+            w->pinv = 0;
+            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : 1, plain ? 0 : 1));
+            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, plain ? QS_F64 : QS_F32, plain ? 0 : 1));
             last_prec = plain ? QS_F64 : QS_F32;
             stall = fstall = 0;
             prev_worst = 1e300;
@@ -418,8 +625,8 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         if (worst <= o->tol) {
             if (last_prec == QS_F64) { *conv = 1; break; }
             // confirm with the FP64 operator (and an FP64-orthonormal block) before accepting
-            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, 0));
-            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F64));
+            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, glow, 0));
+            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F64, glow));
             last_prec = QS_F64;
             continue;
         }
@@ -432,12 +639,26 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             } else {
                 const int storage = o->precision == QS_F16 ? QS_D32_F16
                                   : o->precision == QS_BF16 ? QS_D32_BF16 : QS_D32_F32_TILED;
-                if (storage == QS_D32_F32_TILED) CK(qs_d2f(w->blk64[0], w->blk32[0], nullptr, k, w->nr, st));
-                else CK(qs_q16_from_f64(storage, w->blk64[0], w->blk32[0], lat->g.Ns, k, st));
+                // C* pairing: filter k / 2 representatives, their partners complete the
+                // block (the filter is a polynomial in Q^2, which commutes with P)
+                const int kf = pair ? k / 2 : k;
+                const double *src = w->blk64[0];
+                if (pair) {
+                    int sel[32];
+                    QS_TRY(pick_representatives(lat, w, rz, k, sel));
+                    QS_TRY(gather_columns(lat, w, sel, kf, w->blk64[2], nullptr));
+                    src = w->blk64[2];
+                }
+                if (storage == QS_D32_F32_TILED) CK(qs_d2f(src, w->blk32[0], nullptr, kf, w->nr, st));
+                else CK(qs_q16_from_f64(storage, src, w->blk32[0], lat->g.Ns, kf, st));
                 void *Y = nullptr;
-                QS_TRY(cheb_filter(lat, w, m0, k, std::max(2, o->cheb_degree), a, b, storage, &Y));
-                if (storage == QS_D32_F32_TILED) CK(qs_f2d((const float *)Y, w->blk64[2], k, w->nr, st));
-                else CK(qs_f64_from_q16(storage, Y, w->blk64[2], lat->g.Ns, k, st));
+                QS_TRY(cheb_filter(lat, w, m0, kf, std::max(2, o->cheb_degree), a, b, storage, &Y));
+                if (storage == QS_D32_F32_TILED) CK(qs_f2d((const float *)Y, w->blk64[2], kf, w->nr, st));
+                else CK(qs_f64_from_q16(storage, Y, w->blk64[2], lat->g.Ns, kf, st));
+                if (pair) {
+                    CK(qs_partner(w->blk64[2], w->blk64[2] + (size_t)kf * w->nr, lat->g, kf, 1, st));
+                    w->pinv = 1;
+                }
                 std::swap(w->blk64[0], w->blk64[2]);
             }
             ++nf;
@@ -449,20 +670,34 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
                 double q2 = rz->theta_dev[i] * rz->theta_dev[i] + rz->res_dev[i] * rz->res_dev[i];
                 inv[i] = q2 > 0 ? 1.0 / q2 : 0.0;
             }
-            CK(cudaMemcpyAsync(DS(w, S_COEF), inv, k * sizeof(double), cudaMemcpyHostToDevice, st));
-            CK(qs_scaled_copy(w->blk64[2], w->blk64[0], DS(w, S_COEF), k, w->nr, st));
             // solve accuracy tied to the absolute residual the target needs
             double tsol = std::max(1e-13, std::min(1e-2, 0.05 * worst * fabs(rz->theta[0])));
-            int s = solve_q2_mixed(lat, w, m0, k, w->blk64[0], w->blk64[2], w->blk64[4], w->blk64[5], tsol);
-            if (s != QS_OK && s != QS_ENOCONV) return s;
+            if (pair) {
+                // Q^-2 commutes with P: solve for k / 2 representatives, partners complete
+                const int h = k / 2;
+                int sel[32];
+                QS_TRY(pick_representatives(lat, w, rz, k, sel));
+                QS_TRY(gather_columns(lat, w, sel, h, w->blk64[3], nullptr));
+                QS_TRY(gather_columns(lat, w, sel, h, w->blk64[2], inv));
+                int s = solve_q2_mixed(lat, w, m0, h, w->blk64[3], w->blk64[2], w->blk64[4], w->blk64[5], tsol);
+                if (s != QS_OK && s != QS_ENOCONV) return s;
+                CK(qs_partner(w->blk64[2], w->blk64[2] + (size_t)h * w->nr, lat->g, h, 1, st));
+                w->pinv = 1;
+            } else {
+                CK(cudaMemcpyAsync(DS(w, S_COEF), inv, k * sizeof(double), cudaMemcpyHostToDevice, st));
+                CK(qs_scaled_copy(w->blk64[2], w->blk64[0], DS(w, S_COEF), k, w->nr, st));
+                int s = solve_q2_mixed(lat, w, m0, k, w->blk64[0], w->blk64[2], w->blk64[4], w->blk64[5], tsol);
+                if (s != QS_OK && s != QS_ENOCONV) return s;
+            }
             std::swap(w->blk64[0], w->blk64[2]);
             ++nref;
         }
         // FP32 operator, Gram and rotation while the block is far from converged (its
         // residuals are then far above FP32 rounding); FP64 from the refinement on
         last_prec = (plain || refine || worst < 1e-3) ? QS_F64 : QS_F32;
-        QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, last_prec == QS_F32));
-        QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, last_prec));
+        const int f32 = last_prec == QS_F32;
+        QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, f32 || glow, f32));
+        QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, last_prec, glow));
         double nw = 0;
         for (int i = 0; i < o->nwant; ++i) nw = std::max(nw, rel(i));
         if (refine) { if (nw > 0.97 * prev_worst) ++stall; else stall = 0; }

@@ -124,3 +124,61 @@ def test_16bit_filter_on_tiny_workload_golden(qs):
     ev, rs, st = lat.lowmodes_at_mass(pt["m0"], opts)
     check_against(ev, rs, np.array(pt["lowest_abs_sorted_eigs_Q"]), 8)
     lat.close()
+
+
+def test_cstar_partner_of_eigenvectors(qs):
+    """qs_cstar_partner maps an eigenvector of Q (oracle) to an orthogonal eigenvector
+    with the same eigenvalue (Sec. 3), equal to the oracle's C T gamma_5 v^*, and P^2 = -1."""
+    import torch
+    from oracle.dirac import gamma5_vec
+    cfg = make_config(T=4, L=2, eps=0.9, theta_sigma=0.4, csw_su3=1.3, csw_u1=0.8, seed=5)
+    op = WilsonDirac(cfg)
+    lat = lattice(qs, cfg)
+    m0 = -0.6
+    w, V = np.linalg.eigh(op.dense_Q(m0))
+    v = np.ascontiguousarray(V[:, [0, 5, 100]].T)
+    x = torch.from_numpy(v.view(np.float64).copy()).cuda().reshape(-1)
+    y = torch.empty_like(x)
+    qs.cstar_partner(lat.h, x, y)
+    u = y.cpu().numpy().view(np.complex128).reshape(3, -1)
+    CT = op.CT_matrix()
+    Q = op.dense_Q(m0)
+    for i, col in enumerate([0, 5, 100]):
+        ref = CT @ gamma5_vec(v[i].conj())
+        assert np.abs(u[i] - ref).max() < 1e-14
+        assert np.abs(Q @ u[i] - w[col] * u[i]).max() < 1e-11
+        assert abs(np.vdot(v[i], u[i])) < 1e-11
+    z = torch.empty_like(x)
+    qs.cstar_partner(lat.h, y, z)
+    assert torch.allclose(z, -x, atol=0, rtol=0)
+    # the tiled layout gives the same map
+    xt, yt = qs.to_tiled(x, cfg.n_sites), torch.empty_like(x)
+    qs.cstar_partner(lat.h, xt, yt, tiled=True)
+    assert torch.equal(qs.from_tiled(yt, cfg.n_sites), y)
+    lat.close()
+
+
+def test_graph_replayed_filter_on_own_stream(qs):
+    """A handle with its own stream captures the filter loop as a CUDA graph after the
+    first pass and replays it; the low eigenvalues still match the dense oracle (4^4
+    golden), with FP16 and FP32 filter storage, and a gauge reload invalidates the graph."""
+    import torch
+    g = json.load(open(os.path.join(HERE, "golden", "tiny_4x4x4x4_seed0.json")))
+    cfg = make_config(seed=0, **WORKLOADS["tiny_4x4x4x4"])
+    st = torch.cuda.Stream()
+    lat = qs.Lattice(cfg.L, cfg.T, stream=st)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    for precision in (2, 1):
+        opts = qs.eig_default_opts(k=16, nwant=8, tol=1e-9, cheb_degree=24, precision=precision, warm_start=0)
+        for pt in g["points"][:2]:
+            ev, rs, stats = lat.lowmodes_at_mass(pt["m0"], opts)
+            check_against(ev, rs, np.array(pt["lowest_abs_sorted_eigs_Q"]), 8)
+            assert stats["filter_passes"] >= 2
+    # a different field on the same handle: graphs captured with the old one are not reused
+    other = make_config(T=4, L=4, eps=0.5, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0, seed=2)
+    lat.load_gauge(other.su3, other.theta, other.csw_su3, other.csw_u1)
+    ev, rs, _ = lat.lowmodes_at_mass(-0.2, qs.eig_default_opts(k=16, nwant=8, tol=1e-9, warm_start=0, precision=2))
+    s = np.sort(ev[:8])
+    assert np.allclose(s[0::2], s[1::2], rtol=1e-9, atol=1e-13)
+    assert np.all(rs[:8] <= 1e-9 * np.abs(ev[:8]) + 1e-12)
+    lat.close()

@@ -61,3 +61,31 @@ def test_large_mass_is_positive_in_one_step(qs):
     s, rep = lat.pfaffian_sign(3 * (1.9 + 1.0) + 0.5, qs.sign_default_opts())
     assert s == 1 and rep["n"] == 1
     lat.close()
+
+
+def test_batched_sign_matches_single_flows(qs):
+    """qs_pfaffian_sign_batch over configurations of different volumes, each handle on
+    its own stream: every sign equals the dense oracle's and the single-flow result."""
+    import torch
+    cfgs = [make_config(T=4, L=2, eps=2.0, theta_sigma=0.3, csw_su3=1.5, csw_u1=1.0, seed=2),
+            make_config(seed=0, **WORKLOADS["tiny_4x4x4x4"]),
+            make_config(T=6, L=2, eps=1.2, theta_sigma=0.3, csw_su3=1.5, csw_u1=1.0, seed=4)]
+    masses = [-1.65, -2.005, -0.5]
+    streams = [torch.cuda.Stream() for _ in cfgs]
+    lats = []
+    for c, st in zip(cfgs, streams):
+        lat = qs.Lattice(c.L, c.T, stream=st)
+        lat.load_gauge(c.su3, c.theta, c.csw_su3, c.csw_u1)
+        lats.append(lat)
+    opts = qs.sign_default_opts(eig={"k": 16, "nwant": 2, "tol": 1e-6, "cheb_degree": 24})
+    out = qs.pfaffian_sign_batch(lats, masses, opts)
+    for (s, status, rep), lat, m, c in zip(out, lats, masses, cfgs):
+        assert status == 0
+        ref = sign_by_eigencount(WilsonDirac(c), m) if c.n_sites * 12 <= 2000 else None
+        if ref is not None:
+            assert s == ref, (m, s, ref)
+        s1, _ = lat.pfaffian_sign(m, opts)
+        assert s1 == s
+    assert out[1][0] == -1          # the 4^4 golden mass -2.005 has W_sgn = -1
+    for lat in lats:
+        lat.close()
