@@ -63,17 +63,20 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def measured_traffic(kind, nrhs):
-    """DRAM bytes per launch of the operator from the committed ncu summary, if that
-    capture was of the current kernel source and the same launch shape; else None."""
+def measured_traffic(kind, algorithmic_bytes_per_launch):
+    """DRAM bytes per launch of the operator, from the committed ncu summary of one launch
+    of the current kernel source: the capture's ratio of DRAM bytes (read + write) to
+    algorithmic bytes, applied to this launch's algorithmic bytes (traffic scales with the
+    sites and right-hand sides a launch processes).  None if no capture of the current
+    source and storage exists."""
     p = os.path.join(ROOT, "profiles", "dslash32_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(f"{kind}_nrhs{nrhs}")
+    e = d.get(kind)
     if not e or d.get("source_sha256") != kernel_source_hash():
         return None
-    return e["dram_bytes_per_launch_full_size"]
+    return algorithmic_bytes_per_launch * e["dram_bytes"] / e["algorithmic_bytes"]
 
 
 def peaks():
@@ -430,7 +433,8 @@ def run_sign(args):
                     "cg_iterations": rep["cg_iterations"],
                     "operator_ms_share_of_step": {n: p["ms"] / total_ms for n, p in prof.items() if p["ms"] > 0}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(dname, args.k),
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(dname, dom["bytes"] / max(1, dom["launches"])),
                      "kernel": f"dslash32_kernel ({dname} storage, FP32 arithmetic)" if dname != "f64"
                      else "dslash_kernel<double>",
                      "launches": dom["launches"], "avg_launch_us": 1e3 * dom["ms"] / max(1, dom["launches"]),
@@ -445,7 +449,7 @@ def run_sign(args):
     if rank == 0 and not args.no_extras:
         forms = {f"mixed_{args.eig_prec}_filter": {"s_per_config": ms_step / 1e3, "sign": sign, "masses": rep["n"]}}
         for name, prec in (("mixed_f32_filter", 1), ("plain_fp64", 0)):
-            if name.startswith("plain") and args.no_plain:
+            if name.startswith("plain") and not args.plain_sign:
                 continue
             o = sign_opts(qs, args, prec)
             torch.cuda.synchronize()
@@ -456,6 +460,23 @@ def run_sign(args):
                                "dslash_f64": r["dslash_f64"], "dslash_f32_arith": r["dslash_f32"]}
             except qs.QStarError as e:
                 forms[name] = {"error": str(e)}
+        # one cold low-mode solve at the target mass, mixed (16-bit filter) vs plain FP64,
+        # at equal eigenvalue tolerance
+        cmp = {}
+        for name, prec in (("mixed_f16_filter", 2), ("plain_fp64", 0)):
+            eo = qs.eig_default_opts(k=16, nwant=2, tol=1e-8, cheb_degree=args.degree, warm_start=0,
+                                     max_iter=400, precision=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev, rs, st = lat.lowmodes_at_mass(m0, eo, allow_noconv=True)
+            torch.cuda.synchronize()
+            cmp[name] = {"s": time.perf_counter() - t0, "lambda_bar": abs(float(ev[0])), "resid": float(rs[0]),
+                         "status": st["status"], "passes": st["iterations"], "dslash_f64": st["dslash_f64"],
+                         "dslash_f32_arith": st["dslash_f32"]}
+        cmp["speedup_mixed_over_plain"] = cmp["plain_fp64"]["s"] / cmp["mixed_f16_filter"]["s"]
+        cmp["lambda_bar_rel_diff"] = abs(cmp["mixed_f16_filter"]["lambda_bar"] - cmp["plain_fp64"]["lambda_bar"]) / \
+            cmp["plain_fp64"]["lambda_bar"]
+        out["eigensolve_mixed_vs_plain_fp64"] = cmp
         base = forms.get("plain_fp64", {}).get("s_per_config")
         if base:
             for f in forms.values():
@@ -529,7 +550,7 @@ def run_op_only(args):
                    "l2": "inputs rotated over buffer sets larger than L2",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                     "traffic": measured_traffic(prec, R), "peak_source": f"{src} hbm_gbs (of measured)",
+                     "traffic": measured_traffic(prec, bytes_per_launch), "peak_source": f"{src} hbm_gbs (of measured)",
                      "bytes_model": f"{op_bytes_per_site(R, prec)} B/site"},
         "e2e": {"value": e2e, "unit": "GB/s", "h2d_bytes_per_step": hx.numel() * hx.element_size(),
                 "d2h_bytes_per_step": hy.numel() * hy.element_size()},
@@ -563,7 +584,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other forms and the 32^3x64 lines")
-    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 sign computation")
+    ap.add_argument("--plain-sign", action="store_true",
+                    help="also time W_sgn in the plain FP64 form (several minutes on 16^3x32)")
     ap.add_argument("--no-big", action="store_true", help="skip the 32^3x64 lines")
     ap.add_argument("--no-big-eig", action="store_true", help="skip the 32^3x64 low-mode solve")
     args = ap.parse_args()

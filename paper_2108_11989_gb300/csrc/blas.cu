@@ -73,18 +73,19 @@ __global__ void dot_part(const R *__restrict__ a, const R *__restrict__ b, int64
     }
 }
 
-__global__ void resid_part(const double *__restrict__ a, const double *__restrict__ b, const double *theta,
+template <typename R>
+__global__ void resid_part(const R *__restrict__ a, const R *__restrict__ b, const double *theta,
                            int64_t nr, double *part)
 {
-    const double *x = a + (int64_t)blockIdx.y * nr;
-    const double *y = b + (int64_t)blockIdx.y * nr;
-    double t = theta[blockIdx.y];
-    double acc = 0;
+    const R *x = a + (int64_t)blockIdx.y * nr;
+    const R *y = b + (int64_t)blockIdx.y * nr;
+    const R t = (R)theta[blockIdx.y];
+    R acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr; i += (int64_t)gridDim.x * blockDim.x) {
-        double d = x[i] - t * y[i];
+        R d = x[i] - t * y[i];
         acc += d * d;
     }
-    double s = block_sum(acc);
+    double s = block_sum((double)acc);
     if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
@@ -96,10 +97,21 @@ __global__ void resid_part(const double *__restrict__ a, const double *__restric
 // shared memory at the end, in a fixed order.  LOWP: values rounded to FP32, products
 // and the sum over one chunk in FP32, chunk sums added in FP64.
 #define GE 64
-template <bool LOWP>
-__global__ void __launch_bounds__(256) gram_tile_kernel(const double2 *__restrict__ A, int ka,
-                                                        const double2 *__restrict__ B, int kb, int64_t nc,
-                                                        double *part)
+// (hi, lo) += x, with hi + lo exact to the rounding of the final add (Knuth's two-sum)
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+{
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+__device__ __forceinline__ void two_sum_acc(double &hi, double &lo, double x) { hi += x; }
+
+template <bool LOWP, typename TIn = double2>
+__global__ void __launch_bounds__(256, LOWP ? 2 : 1) gram_tile_kernel(const TIn *__restrict__ A_, int ka,
+                                                           const TIn *__restrict__ B_, int kb, int64_t nc,
+                                                           double *part)
 {
     typedef typename std::conditional<LOWP, float2, double2>::type V2;
     typedef typename std::conditional<LOWP, float, double>::type T;
@@ -112,54 +124,94 @@ __global__ void __launch_bounds__(256) gram_tile_kernel(const double2 *__restric
     const int tile = t % ntile, eg = t / ntile;
     const bool active = eg < eg_n;
     const int i0 = 4 * (tile / tj_n), j0 = 4 * (tile % tj_n);
-    double acc[4][4][2];
+    // running totals: FP64 (FP64 products), or an FP32 (hi, lo) pair per real sum kept
+    // exact to ~2^-48 by Knuth's two-sum (FP32 products: GB300's FP64 pipe is too slow
+    // for a per-chunk FP64 add)
+    typedef typename std::conditional<LOWP, float, double>::type A;
+    A acc[4][4][2], accl[4][4][2];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+        for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = accl[a][b][0] = accl[a][b][1] = (A)0;
     const int64_t nch = (nc + GE - 1) / GE;
+    const int nq = kk * GE;
     for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
         const int64_t e0 = ch * GE;
         __syncthreads();
-        for (int q = t; q < kk * GE; q += 256) {
-            const int v = q / GE, e = q % GE;
-            const int64_t idx = e0 + e;
-            double2 val = make_double2(0, 0);
-            if (idx < nc) val = v < ka ? A[(int64_t)v * nc + idx] : B[(int64_t)(v - ka) * nc + idx];
-            V2 x;
-            x.x = (T)val.x;
-            x.y = (T)val.y;
-            sv[e * row + v] = x;
+        // staging: SU independent loads in flight per thread before their stores
+        constexpr int SU = LOWP ? 4 : 8;
+        for (int q0 = t; q0 < nq; q0 += 256 * SU) {
+            TIn val[SU];
+#pragma unroll
+            for (int u = 0; u < SU; ++u) {
+                const int q = q0 + 256 * u;
+                val[u].x = 0;
+                val[u].y = 0;
+                if (q < nq) {
+                    const int v = q / GE, e = q % GE;
+                    const int64_t idx = e0 + e;
+                    if (idx < nc) val[u] = v < ka ? __ldg(A_ + (int64_t)v * nc + idx) : __ldg(B_ + (int64_t)(v - ka) * nc + idx);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SU; ++u) {
+                const int q = q0 + 256 * u;
+                if (q < nq) {
+                    V2 x;
+                    x.x = (T)val[u].x;
+                    x.y = (T)val[u].y;
+                    sv[(q % GE) * row + q / GE] = x;
+                }
+            }
         }
         __syncthreads();
         if (!active) continue;
-        T cr[4][4], ci[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) cr[a][b] = ci[a][b] = (T)0;
-        for (int e = eg; e < GE; e += eg_n) {
-            const V2 *r = sv + e * row;
-            V2 x[4], y[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) x[a] = (i0 + a < ka) ? r[i0 + a] : V2{(T)0, (T)0};
-#pragma unroll
-            for (int b = 0; b < 4; ++b) y[b] = (j0 + b < kb) ? r[ka + j0 + b] : V2{(T)0, (T)0};
+        if constexpr (LOWP) {
+            // FP32 sums over the chunk, added to the (hi, lo) totals once per chunk
+            float cr[4][4], ci[4][4];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {   // conj(x) y
-                    cr[a][b] = fma(x[a].x, y[b].x, fma(x[a].y, y[b].y, cr[a][b]));
-                    ci[a][b] = fma(x[a].x, y[b].y, fma(-x[a].y, y[b].x, ci[a][b]));
-                }
-        }
+                for (int b = 0; b < 4; ++b) cr[a][b] = ci[a][b] = 0.f;
+            for (int e = eg; e < GE; e += eg_n) {
+                const V2 *r = sv + e * row;
+                V2 x[4], y[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a) x[a] = (i0 + a < ka) ? r[i0 + a] : V2{0.f, 0.f};
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                acc[a][b][0] += (double)cr[a][b];
-                acc[a][b][1] += (double)ci[a][b];
+                for (int b = 0; b < 4; ++b) y[b] = (j0 + b < kb) ? r[ka + j0 + b] : V2{0.f, 0.f};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {   // conj(x) y
+                        cr[a][b] = fmaf(x[a].x, y[b].x, fmaf(x[a].y, y[b].y, cr[a][b]));
+                        ci[a][b] = fmaf(x[a].x, y[b].y, fmaf(-x[a].y, y[b].x, ci[a][b]));
+                    }
             }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    two_sum_acc(acc[a][b][0], accl[a][b][0], cr[a][b]);
+                    two_sum_acc(acc[a][b][1], accl[a][b][1], ci[a][b]);
+                }
+        } else {
+            for (int e = eg; e < GE; e += eg_n) {
+                const V2 *r = sv + e * row;
+                V2 x[4], y[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) x[a] = (i0 + a < ka) ? r[i0 + a] : V2{0.0, 0.0};
+#pragma unroll
+                for (int b = 0; b < 4; ++b) y[b] = (j0 + b < kb) ? r[ka + j0 + b] : V2{0.0, 0.0};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {   // conj(x) y
+                        acc[a][b][0] = fma(x[a].x, y[b].x, fma(x[a].y, y[b].y, acc[a][b][0]));
+                        acc[a][b][1] = fma(x[a].x, y[b].y, fma(-x[a].y, y[b].x, acc[a][b][1]));
+                    }
+            }
+        }
     }
     // sum the element classes of each tile (fixed order), reusing the staging buffer
     __syncthreads();
@@ -171,8 +223,10 @@ __global__ void __launch_bounds__(256) gram_tile_kernel(const double2 *__restric
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     double *d = red + tile * 32 + (a * 4 + b) * 2;
-                    if (c == 0) { d[0] = acc[a][b][0]; d[1] = acc[a][b][1]; }
-                    else { d[0] += acc[a][b][0]; d[1] += acc[a][b][1]; }
+                    const double v0 = (double)acc[a][b][0] + (double)accl[a][b][0];
+                    const double v1 = (double)acc[a][b][1] + (double)accl[a][b][1];
+                    if (c == 0) { d[0] = v0; d[1] = v1; }
+                    else { d[0] += v0; d[1] += v1; }
                 }
         }
         __syncthreads();
@@ -192,15 +246,15 @@ __global__ void __launch_bounds__(256) gram_tile_kernel(const double2 *__restric
 // up to RJ output vectors, the coefficients read from shared memory (the same word for
 // all threads of a warp); each W value it loads feeds RJ multiply-adds.  LOWP: values and
 // coefficients rounded to FP32, the sums in FP32.
-#define RJ 16
 #define RE 2
-template <bool LOWP>
-__global__ void __launch_bounds__(256) rotate_tile_kernel(const double2 *__restrict__ W, int ka,
-                                                          const double2 *__restrict__ C, int kc, int64_t nc,
-                                                          double2 *__restrict__ V)
+template <bool LOWP, typename TIn = double2, typename TOut = double2>
+__global__ void __launch_bounds__(256, 2) rotate_tile_kernel(const TIn *__restrict__ W, int ka,
+                                                             const double2 *__restrict__ C, int kc, int64_t nc,
+                                                             TOut *__restrict__ V)
 {
     typedef typename std::conditional<LOWP, float2, double2>::type V2;
     typedef typename std::conditional<LOWP, float, double>::type T;
+    constexpr int RJ = LOWP ? 16 : 8;   // output columns per pass (register budget)
     extern __shared__ __align__(16) unsigned char rsm_raw[];
     V2 *cs = reinterpret_cast<V2 *>(rsm_raw);         // [ka][kc]
     for (int q = threadIdx.x; q < ka * kc; q += blockDim.x) {
@@ -218,24 +272,34 @@ __global__ void __launch_bounds__(256) rotate_tile_kernel(const double2 *__restr
             for (int u = 0; u < RE; ++u)
 #pragma unroll
                 for (int jj = 0; jj < RJ; ++jj) ar[u][jj] = ai[u][jj] = (T)0;
-            for (int i = 0; i < ka; ++i) {
-                T wr[RE], wi[RE];
+            for (int i0 = 0; i0 < ka; i0 += 4) {
+                // four input vectors' values loaded together (independent loads in flight)
+                T wr[4][RE], wi[4][RE];
 #pragma unroll
-                for (int u = 0; u < RE; ++u) {
-                    const int64_t e = base + (int64_t)u * blockDim.x;
-                    double2 w = e < nc ? __ldg(W + (int64_t)i * nc + e) : make_double2(0, 0);
-                    wr[u] = (T)w.x;
-                    wi[u] = (T)w.y;
-                }
-                const V2 *crow = cs + i * kc + j0;
+                for (int di = 0; di < 4; ++di)
 #pragma unroll
-                for (int jj = 0; jj < RJ; ++jj) {
-                    if (j0 + jj < kc) {
-                        const V2 c = crow[jj];
+                    for (int u = 0; u < RE; ++u) {
+                        const int64_t e = base + (int64_t)u * blockDim.x;
+                        TIn w;
+                        w.x = 0;
+                        w.y = 0;
+                        if (e < nc && i0 + di < ka) w = __ldg(W + (int64_t)(i0 + di) * nc + e);
+                        wr[di][u] = (T)w.x;
+                        wi[di][u] = (T)w.y;
+                    }
 #pragma unroll
-                        for (int u = 0; u < RE; ++u) {
-                            ar[u][jj] = fma(wr[u], c.x, fma(-wi[u], c.y, ar[u][jj]));
-                            ai[u][jj] = fma(wr[u], c.y, fma(wi[u], c.x, ai[u][jj]));
+                for (int di = 0; di < 4; ++di) {
+                    if (i0 + di >= ka) break;
+                    const V2 *crow = cs + (i0 + di) * kc + j0;
+#pragma unroll
+                    for (int jj = 0; jj < RJ; ++jj) {
+                        if (j0 + jj < kc) {
+                            const V2 c = crow[jj];
+#pragma unroll
+                            for (int u = 0; u < RE; ++u) {
+                                ar[u][jj] = fma(wr[di][u], c.x, fma(-wi[di][u], c.y, ar[u][jj]));
+                                ai[u][jj] = fma(wr[di][u], c.y, fma(wi[di][u], c.x, ai[u][jj]));
+                            }
                         }
                     }
                 }
@@ -246,7 +310,12 @@ __global__ void __launch_bounds__(256) rotate_tile_kernel(const double2 *__restr
 #pragma unroll
                     for (int u = 0; u < RE; ++u) {
                         const int64_t e = base + (int64_t)u * blockDim.x;
-                        if (e < nc) V[(int64_t)(j0 + jj) * nc + e] = make_double2((double)ar[u][jj], (double)ai[u][jj]);
+                        if (e < nc) {
+                            TOut o;
+                            o.x = ar[u][jj];
+                            o.y = ai[u][jj];
+                            V[(int64_t)(j0 + jj) * nc + e] = o;
+                        }
                     }
         }
     }
@@ -278,10 +347,11 @@ __global__ void axpy_f2d_kernel(double *__restrict__ x, const float *__restrict_
         a[i] += c * (double)b[i];
 }
 
-__global__ void scale_cols_kernel(double *x, const double *scale, int64_t nr)
+template <typename R>
+__global__ void scale_cols_kernel(R *x, const double *scale, int64_t nr)
 {
-    double c = scale[blockIdx.y];
-    double *a = x + (int64_t)blockIdx.y * nr;
+    const R c = (R)scale[blockIdx.y];
+    R *a = x + (int64_t)blockIdx.y * nr;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr; i += (int64_t)gridDim.x * blockDim.x)
         a[i] *= c;
 }
@@ -435,15 +505,20 @@ cudaError_t qs_dot(const R *a, const R *b, int k, int64_t nr, double *part, doub
 template cudaError_t qs_dot<float>(const float *, const float *, int, int64_t, double *, double *, cudaStream_t);
 template cudaError_t qs_dot<double>(const double *, const double *, int, int64_t, double *, double *, cudaStream_t);
 
-cudaError_t qs_resid2(const double *a, const double *b, const double *theta, int k, int64_t nr,
+template <typename R>
+cudaError_t qs_resid2(const R *a, const R *b, const double *theta, int k, int64_t nr,
                       double *part, double *out, cudaStream_t st)
 {
     dim3 g(QS_RED_BLOCKS, k);
-    resid_part<<<g, QS_RED_THREADS, 0, st>>>(a, b, theta, nr, part);
+    resid_part<R><<<g, QS_RED_THREADS, 0, st>>>(a, b, theta, nr, part);
     finalize_sum<<<k, 256, 0, st>>>(part, QS_RED_BLOCKS, 1, out);
     qs_note_launches(2);
     return cudaGetLastError();
 }
+template cudaError_t qs_resid2<double>(const double *, const double *, const double *, int, int64_t, double *,
+                                       double *, cudaStream_t);
+template cudaError_t qs_resid2<float>(const float *, const float *, const double *, int, int64_t, double *, double *,
+                                      cudaStream_t);
 
 cudaError_t qs_gram(const double *A, int ka, const double *B, int kb, int64_t nr, double *part,
                     double2 *G, cudaStream_t st, int lowp)
@@ -487,6 +562,45 @@ cudaError_t qs_rotate(const double *W, int ka, const double2 *C, int kc, int64_t
     return cudaGetLastError();
 }
 
+// the same contractions on FP32 blocks (products and per-chunk sums in FP32)
+cudaError_t qs_gram32(const float *A, int ka, const float *B, int kb, int64_t nr, double *part, double2 *G,
+                      cudaStream_t st)
+{
+    if (ka < 1 || kb < 1 || ka > 64 || kb > 64) return cudaErrorInvalidValue;
+    int64_t nc = nr / 2;
+    const int row = ka + kb + 1;
+    const size_t stage = (size_t)GE * row * sizeof(float2);
+    const size_t red = (size_t)((ka + 3) / 4) * ((kb + 3) / 4) * 32 * sizeof(double);
+    const size_t sm = stage > red ? stage : red;
+    static std::once_flag attr;
+    std::call_once(attr, [] {
+        cudaFuncSetAttribute(gram_tile_kernel<true, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    });
+    int64_t nch = (nc + GE - 1) / GE;
+    int nb = (int)(nch < QS_RED_BLOCKS ? nch : QS_RED_BLOCKS);
+    gram_tile_kernel<true, float2><<<nb, 256, sm, st>>>((const float2 *)A, ka, (const float2 *)B, kb, nc, part);
+    finalize_sum<<<2 * ka * kb, 256, 0, st>>>(part, nb, 1, reinterpret_cast<double *>(G));
+    qs_note_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t qs_rotate32(const float *W, int ka, const double2 *C, int kc, int64_t nr, float *V, cudaStream_t st)
+{
+    if (ka < 1 || kc < 1 || ka > 64 || kc > 64) return cudaErrorInvalidValue;
+    int64_t nc = nr / 2;
+    size_t sm = (size_t)ka * kc * sizeof(float2);
+    static std::once_flag attr;
+    std::call_once(attr, [] {
+        cudaFuncSetAttribute(rotate_tile_kernel<true, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             64 * 64 * 8);
+    });
+    int64_t blocks = (nc + 256 * RE - 1) / (256 * RE);
+    int nb = (int)(blocks < 4 * 152 ? blocks : 4 * 152);
+    rotate_tile_kernel<true, float2, float2><<<nb, 256, sm, st>>>((const float2 *)W, ka, C, kc, nc, (float2 *)V);
+    qs_note_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t qs_d2f(const double *x, float *y, const double *scale, int k, int64_t nr, cudaStream_t st)
 {
     dim3 g(grid_for(nr) / k + 1, k);
@@ -511,13 +625,16 @@ cudaError_t qs_axpy_f2d(double *x, const float *e, const double *coef, int k, in
     return cudaGetLastError();
 }
 
-cudaError_t qs_scale_cols(double *x, const double *scale, int k, int64_t nr, cudaStream_t st)
+template <typename R>
+cudaError_t qs_scale_cols(R *x, const double *scale, int k, int64_t nr, cudaStream_t st)
 {
     dim3 g(grid_for(nr) / k + 1, k);
-    scale_cols_kernel<<<g, 256, 0, st>>>(x, scale, nr);
+    scale_cols_kernel<R><<<g, 256, 0, st>>>(x, scale, nr);
     qs_note_launches(1);
     return cudaGetLastError();
 }
+template cudaError_t qs_scale_cols<double>(double *, const double *, int, int64_t, cudaStream_t);
+template cudaError_t qs_scale_cols<float>(float *, const double *, int, int64_t, cudaStream_t);
 
 cudaError_t qs_scaled_copy(double *x, const double *b, const double *coef, int k, int64_t nr, cudaStream_t st)
 {

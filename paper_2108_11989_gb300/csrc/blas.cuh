@@ -11,8 +11,9 @@ cudaError_t qs_norm2(const R *v, int k, int64_t nr, double *part, double *out, c
 // out[r] = <a_r, b_r> (complex, conj on a), out as [k][2]
 template <typename R>
 cudaError_t qs_dot(const R *a, const R *b, int k, int64_t nr, double *part, double *out, cudaStream_t st);
-// out[r] = || a_r - theta[r] b_r ||^2 (FP64 vectors, theta on device)
-cudaError_t qs_resid2(const double *a, const double *b, const double *theta, int k, int64_t nr,
+// out[r] = || a_r - theta[r] b_r ||^2 (FP64 or FP32 vectors, FP64 sum, theta on device)
+template <typename R>
+cudaError_t qs_resid2(const R *a, const R *b, const double *theta, int k, int64_t nr,
                       double *part, double *out, cudaStream_t st);
 // G[i][j] = <A_i, B_j>, i < ka, j < kb, complex row-major [ka][kb] (FP64 vectors);
 // lowp: products and per-chunk sums in FP32, chunk sums accumulated in FP64
@@ -22,6 +23,10 @@ cudaError_t qs_gram(const double *A, int ka, const double *B, int kb, int64_t nr
 // lowp: the k-term sums in FP32
 cudaError_t qs_rotate(const double *W, int ka, const double2 *C, int kc, int64_t nr, double *V,
                       cudaStream_t st, int lowp = 0);
+// the Gram matrix and the rotation on FP32 blocks (FP32 products, FP64 Gram totals)
+cudaError_t qs_gram32(const float *A, int ka, const float *B, int kb, int64_t nr, double *part, double2 *G,
+                      cudaStream_t st);
+cudaError_t qs_rotate32(const float *W, int ka, const double2 *C, int kc, int64_t nr, float *V, cudaStream_t st);
 // y_r = (float)(x_r * scale[r])  (scale on device, may be NULL for 1)
 cudaError_t qs_d2f(const double *x, float *y, const double *scale, int k, int64_t nr, cudaStream_t st);
 // y_r = (double) x_r
@@ -36,15 +41,17 @@ cudaError_t qs_cheb_step(R *ynew, const R *ay, const R *y, const R *x, double c,
 template <typename R>
 cudaError_t qs_axpby(double a, const R *x, double b, R *y, int64_t n, cudaStream_t st);
 // x_r *= scale[r] (device)
-cudaError_t qs_scale_cols(double *x, const double *scale, int k, int64_t nr, cudaStream_t st);
+template <typename R>
+cudaError_t qs_scale_cols(R *x, const double *scale, int k, int64_t nr, cudaStream_t st);
 // Gaussian entries from a counter-based hash of (seed, index)
 cudaError_t qs_fill_gauss(double *x, int64_t n, uint64_t seed, cudaStream_t st);
 // x_r = b_r * coef[r] (coef on device)
 cudaError_t qs_scaled_copy(double *x, const double *b, const double *coef, int k, int64_t nr, cudaStream_t st);
 // out[r] = 1 / sqrt(in[r]) (0 stays 0), or theta^-2 style maps, on device
 cudaError_t qs_map_scalars(const double *in, double *out, int k, int mode, cudaStream_t st);
-// C* partner map P v = C T gamma_5 v^* of k FP64 vectors (partner.cu); in != out
+// C* partner map P v = C T gamma_5 v^* of k FP64 or FP32 vectors (partner.cu); in != out
 cudaError_t qs_partner(const double *in, double *out, const Geom &g, int k, int tiled, cudaStream_t st);
+cudaError_t qs_partner32(const float *in, float *out, const Geom &g, int k, cudaStream_t st);
 // single-CTA dense kernels (k <= 64)
 cudaError_t qs_chol_rinv(const double2 *G, int k, double2 *Rinv, int *info, cudaStream_t st);
 cudaError_t qs_herm_eig(const double2 *H, int k, double *evals, double2 *Y, int *info, cudaStream_t st);

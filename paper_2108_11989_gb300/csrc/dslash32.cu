@@ -47,6 +47,7 @@ __device__ __forceinline__ cf cfma(cf a, cf b, cf c)
 // ---- storage formats ------------------------------------------------------
 struct StF32Tiled {
     static constexpr int64_t kBytesPerSite = 96;
+    static constexpr bool kScaled = false;
     __device__ static void ld(const char *__restrict__ base, int s, cf v[12])
     {
         const cf *b = reinterpret_cast<const cf *>(base) + ((int64_t)(s >> 4) * 12) * 16 + (s & 15);
@@ -63,6 +64,7 @@ struct StF32Tiled {
 
 struct StF32Canon {
     static constexpr int64_t kBytesPerSite = 96;
+    static constexpr bool kScaled = false;
     __device__ static void ld(const char *__restrict__ base, int s, cf v[12])
     {
         const float4 *q = reinterpret_cast<const float4 *>(base) + (int64_t)s * 6;
@@ -86,9 +88,23 @@ struct StF32Canon {
 template <typename H2>
 struct StScaled {
     static constexpr int64_t kBytesPerSite = 52;
+    static constexpr bool kScaled = true;
     static constexpr int kTile = 832;
     __device__ static float2 cvt(H2 h);
     __device__ static H2 pack(float a, float b);
+    // the stored (site-normalised) values and the site's scale
+    __device__ static void ld_raw(const char *__restrict__ base, int s, cf v[12], float *scale)
+    {
+        const char *t = base + (int64_t)(s >> 4) * kTile;
+        const unsigned *w = reinterpret_cast<const unsigned *>(t) + (s & 15);
+        *scale = __ldg(reinterpret_cast<const float *>(t + 768) + (s & 15));
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            unsigned u = __ldg(w + c * 16);
+            H2 h = *reinterpret_cast<H2 *>(&u);
+            v[c] = cvt(h);
+        }
+    }
     __device__ static void ld(const char *__restrict__ base, int s, cf v[12])
     {
         const char *t = base + (int64_t)(s >> 4) * kTile;
@@ -280,9 +296,21 @@ __device__ __forceinline__ void hop(const D32 &a, const Site &c, bool mir, int r
     for (int g = 0; g < G; ++g) {
         if (g < nr) {
             cf v[12];
-            S::ld(a.in + (int64_t)(r0 + g) * a.vbytes, n.s, v);
             cf h[2][3], xx[2][3];
-            project<MU, (STEP > 0)>(v, h);
+            if constexpr (S::kScaled) {
+                // the site's scale commutes with the projection: apply it to the 6
+                // projected components instead of the 12 loaded ones
+                float sc;
+                S::ld_raw(a.in + (int64_t)(r0 + g) * a.vbytes, n.s, v, &sc);
+                project<MU, (STEP > 0)>(v, h);
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) h[q][i] = make_float2(sc * h[q][i].x, sc * h[q][i].y);
+            } else {
+                S::ld(a.in + (int64_t)(r0 + g) * a.vbytes, n.s, v);
+                project<MU, (STEP > 0)>(v, h);
+            }
 #pragma unroll
             for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -376,10 +404,17 @@ __device__ __forceinline__ void site_kernel(const D32 &a, unsigned bx, unsigned 
     }
 }
 
-template <class S, int G, int RL, bool CHEB, int MINB>
-__global__ void __launch_bounds__(128, MINB) dslash32_kernel(const __grid_constant__ D32 a)
+// One-dimensional grid over (site tile, right-hand-side group).  SITE_MAJOR: the groups
+// of a site tile are consecutive blocks, so a tile's links and SW terms leave DRAM once
+// for all right-hand sides (the time-slice window of all of them must then fit in L2);
+// otherwise the groups are outermost (a window of one group only, links re-read per group).
+template <class S, int G, int RL, bool CHEB, int MINB, bool SITE_MAJOR>
+__global__ void __launch_bounds__(128, MINB) dslash32_kernel(const __grid_constant__ D32 a, unsigned ntile,
+                                                             unsigned ngroup)
 {
-    site_kernel<S, G, RL, CHEB>(a, blockIdx.x, blockIdx.y);
+    const unsigned b = blockIdx.x;
+    if (SITE_MAJOR) site_kernel<S, G, RL, CHEB>(a, b / ngroup, b % ngroup);
+    else site_kernel<S, G, RL, CHEB>(a, b % ntile, b / ntile);
 }
 
 // Batched persistent form: work items (lattice i, right-hand-side group, site tile)
@@ -456,26 +491,29 @@ cudaError_t convert_from(int to, const void *in, void *out, int64_t Ns, int k, c
 }
 
 // ---- launch ------------------------------------------------------------------
-template <class S, int G, int RL, bool CHEB, int MINB>
+template <class S, int G, int RL, bool CHEB, int MINB, bool SM>
 cudaError_t launch(const D32 &a, cudaStream_t st)
 {
     constexpr int SPB = 128 / RL;
-    dim3 grid((unsigned)((a.g.Ns + SPB - 1) / SPB), (unsigned)((a.nrhs + RL * G - 1) / (RL * G)));
-    dslash32_kernel<S, G, RL, CHEB, MINB><<<grid, 128, 0, st>>>(a);
+    const unsigned ntile = (unsigned)((a.g.Ns + SPB - 1) / SPB);
+    const unsigned ngroup = (unsigned)((a.nrhs + RL * G - 1) / (RL * G));
+    dslash32_kernel<S, G, RL, CHEB, MINB, SM><<<ntile * ngroup, 128, 0, st>>>(a, ntile, ngroup);
     return cudaGetLastError();
 }
 
-// variant table per storage: (G, RL, min blocks per SM)
+// variant table per storage: (G, RL, min blocks per SM, block order)
 template <class S, bool CHEB>
 cudaError_t launch_variant(int v, const D32 &a, cudaStream_t st)
 {
     switch (v) {
-    case 0: return launch<S, 1, 1, CHEB, 3>(a, st);
-    case 1: return launch<S, 1, 4, CHEB, 3>(a, st);
-    case 2: return launch<S, 1, 4, CHEB, 4>(a, st);
-    case 3: return launch<S, 2, 1, CHEB, 3>(a, st);
-    case 4: return launch<S, 2, 4, CHEB, 3>(a, st);
-    default: return launch<S, 2, 2, CHEB, 3>(a, st);
+    case 0: return launch<S, 1, 1, CHEB, 3, false>(a, st);
+    case 1: return launch<S, 1, 4, CHEB, 4, false>(a, st);
+    case 2: return launch<S, 2, 4, CHEB, 3, false>(a, st);
+    case 3: return launch<S, 1, 8, CHEB, 4, false>(a, st);
+    case 4: return launch<S, 1, 1, CHEB, 3, true>(a, st);
+    case 5: return launch<S, 1, 4, CHEB, 4, true>(a, st);
+    case 6: return launch<S, 2, 1, CHEB, 3, true>(a, st);
+    default: return launch<S, 2, 4, CHEB, 3, true>(a, st);
     }
 }
 
@@ -548,7 +586,7 @@ cudaError_t qs_d32_batch_launch(const D32BatchItem *items, int n, int storage, i
     return e;
 }
 
-int qs_d32_nvariants() { return 6; }
+int qs_d32_nvariants() { return 8; }
 
 int64_t qs_d32_vec_bytes(int storage, int64_t Ns)
 {

@@ -10,8 +10,8 @@
 namespace {
 
 // one thread per (vector, site, colour); TILED: [site / 16][12][site % 16] double2
-template <bool TILED>
-__global__ void partner_kernel(const double2 *__restrict__ in, double2 *__restrict__ out, Geom g, int k)
+template <bool TILED, typename V2 = double2>
+__global__ void partner_kernel(const V2 *__restrict__ in, V2 *__restrict__ out, Geom g, int k)
 {
     const int64_t n = g.Ns * 3 * k;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -23,18 +23,19 @@ __global__ void partner_kernel(const double2 *__restrict__ in, double2 *__restri
     const int64_t row = s / g.L2;
     const int x = (int)(s - row * g.L2);
     const int64_t sp = row * g.L2 + (x >= g.L ? x - g.L : x + g.L);   // T s
-    const double2 *a = in + (int64_t)r * g.Ns * 12;
-    double2 *b = out + (int64_t)r * g.Ns * 12;
+    const V2 *a = in + (int64_t)r * g.Ns * 12;
+    V2 *b = out + (int64_t)r * g.Ns * 12;
     auto at = [&](int64_t site, int comp) -> int64_t {
         return TILED ? ((site >> 4) * 12 + comp) * 16 + (site & 15) : site * 12 + comp;
     };
-    double2 v[4];
+    V2 v[4];
 #pragma unroll
     for (int sp_ = 0; sp_ < 4; ++sp_) v[sp_] = a[at(sp, sp_ * 3 + col)];
-    b[at(s, 0 * 3 + col)] = make_double2(-v[1].y, -v[1].x);
-    b[at(s, 1 * 3 + col)] = make_double2(v[0].y, v[0].x);
-    b[at(s, 2 * 3 + col)] = make_double2(-v[3].y, -v[3].x);
-    b[at(s, 3 * 3 + col)] = make_double2(v[2].y, v[2].x);
+    V2 o;
+    o.x = -v[1].y; o.y = -v[1].x; b[at(s, 0 * 3 + col)] = o;
+    o.x = v[0].y;  o.y = v[0].x;  b[at(s, 1 * 3 + col)] = o;
+    o.x = -v[3].y; o.y = -v[3].x; b[at(s, 2 * 3 + col)] = o;
+    o.x = v[2].y;  o.y = v[2].x;  b[at(s, 3 * 3 + col)] = o;
 }
 
 }  // namespace
@@ -45,6 +46,15 @@ cudaError_t qs_partner(const double *in, double *out, const Geom &g, int k, int 
     const unsigned nb = (unsigned)((n + 255) / 256);
     if (tiled) partner_kernel<true><<<nb, 256, 0, st>>>((const double2 *)in, (double2 *)out, g, k);
     else partner_kernel<false><<<nb, 256, 0, st>>>((const double2 *)in, (double2 *)out, g, k);
+    qs_note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t qs_partner32(const float *in, float *out, const Geom &g, int k, cudaStream_t st)
+{
+    const int64_t n = g.Ns * 3 * k;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    partner_kernel<true, float2><<<nb, 256, 0, st>>>((const float2 *)in, (float2 *)out, g, k);
     qs_note_launches(1);
     return cudaGetLastError();
 }

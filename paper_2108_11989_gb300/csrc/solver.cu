@@ -37,7 +37,9 @@ struct Workspace {
     int k;
     int64_t nr;
     double *blk64[6];     // FP64 blocks [k][nr]
-    float *blk32[5];      // FP32 blocks [k][nr]
+    float *blk32[5];      // FP32 blocks [k][nr]: filter (captured buffers 0-3) and CG work
+    float *f32b[3];       // FP32 basis of the filter stage: V, QV and a rotation target
+    int iv, iq, it3;      // which of f32b holds V, QV and the scratch
     double *part;         // reduction partials
     double2 *G, *Rinv, *Hm, *Ym;
     double *ds;           // device scalars, S_NSLOT slots of 64
@@ -50,6 +52,9 @@ struct Workspace {
 };
 
 #define DS(ws, slot) ((ws)->ds + 64 * (slot))
+static float *V32(Workspace *w);
+static float *QV32(Workspace *w);
+static float *T32(Workspace *w);
 enum { S_TMP = 0, S_THETA = 1, S_COEF = 2, S_RR = 3, S_RR0 = 4, S_PAP = 5, S_BETA = 6, S_ONES = 7, S_RN = 8,
        S_DOT = 9 /* two slots */, S_VN = 11, S_NSLOT = 12 };
 
@@ -61,6 +66,7 @@ static void ws_free(Workspace *w)
     cudaFreeHost(w->coef_host);
     for (int i = 0; i < 6; ++i) cudaFree(w->blk64[i]);
     for (int i = 0; i < 5; ++i) cudaFree(w->blk32[i]);
+    for (int i = 0; i < 3; ++i) cudaFree(w->f32b[i]);
     cudaFree(w->part); cudaFree(w->G); cudaFree(w->Rinv); cudaFree(w->Hm); cudaFree(w->Ym);
     cudaFree(w->ds); cudaFree(w->di);
     cudaFreeHost(w->hp); cudaFreeHost(w->hi);
@@ -89,6 +95,8 @@ static int ws_alloc(qs_lattice *lat, Workspace *w, int k)
     size_t n64 = (size_t)k * w->nr * sizeof(double), n32 = (size_t)k * w->nr * sizeof(float);
     for (int i = 0; i < 6; ++i) CK(cudaMalloc(&w->blk64[i], n64));
     for (int i = 0; i < 5; ++i) CK(cudaMalloc(&w->blk32[i], n32));
+    for (int i = 0; i < 3; ++i) CK(cudaMalloc(&w->f32b[i], n32));
+    w->iv = 0; w->iq = 1; w->it3 = 2;
     CK(cudaMalloc(&w->part, (size_t)QS_RED_BLOCKS * 2 * 64 * 64 * sizeof(double)));
     CK(cudaMalloc(&w->G, 64 * 64 * sizeof(double2)));
     CK(cudaMalloc(&w->Rinv, 64 * 64 * sizeof(double2)));
@@ -179,6 +187,33 @@ static int orthonormalize(qs_lattice *lat, Workspace *w, double *X, double *tmp,
 // be spurious (+lambda and -lambda contaminations averaging to a small theta, with a
 // large r).  The pairs are therefore ordered by <v, Q^2 v> = theta^2 + r^2, which is
 // close to lambda^2 for a genuine pair and large for a spurious one.
+// Ritz values and residual bounds read back from the pinned mirror (slots S_THETA, S_TMP
+// = r^2, S_RN = Q^2 Ritz values) into rz, pairs ordered by theta^2 + r^2
+static int finish_ritz(Workspace *w, int k, Ritz *rz)
+{
+    if (w->hi[64] || w->hi[65]) return QS_ENUMERIC;   // Cholesky-QR broke down
+    if (w->hi[66] || w->hi[67]) return QS_ENOCONV;    // Jacobi hit its sweep cap
+    double th[64], rs[64], key[64];
+    rz->mu_max = 0;
+    for (int i = 0; i < k; ++i) {
+        th[i] = w->hp[64 * S_THETA + i];
+        double r2 = w->hp[64 * S_TMP + i];
+        rs[i] = sqrt(r2 > 0 ? r2 : 0);
+        key[i] = th[i] * th[i] + rs[i] * rs[i];
+        rz->mu_max = std::max(rz->mu_max, fabs(w->hp[64 * S_RN + i]));
+        rz->theta_dev[i] = th[i];
+        rz->res_dev[i] = rs[i];
+        rz->col[i] = i;
+        if (!isfinite(th[i]) || !isfinite(rs[i])) return QS_ENUMERIC;
+    }
+    std::stable_sort(rz->col, rz->col + k, [&](int a, int b) { return key[a] < key[b]; });
+    for (int i = 0; i < k; ++i) {
+        rz->theta[i] = th[rz->col[i]];
+        rz->res[i] = rs[rz->col[i]];
+    }
+    return QS_OK;
+}
+
 // prec: operator precision (FP32 while far from convergence, FP64 otherwise).
 // glow: FP32 products in the Gram matrices (then the block is orthonormal only to ~1e-7
 // and every residual is divided by ||v||); the rotations use FP32 products only with
@@ -217,27 +252,7 @@ static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *
             const double vn = w->hp[64 * S_VN + i];
             w->hp[64 * S_TMP + i] = vn > 0 ? w->hp[64 * S_TMP + i] / vn : INFINITY;
         }
-    if (w->hi[64] || w->hi[65]) return QS_ENUMERIC;   // Cholesky-QR broke down
-    if (w->hi[66] || w->hi[67]) return QS_ENOCONV;    // Jacobi hit its sweep cap
-    double th[64], rs[64], key[64];
-    rz->mu_max = 0;
-    for (int i = 0; i < k; ++i) {
-        th[i] = w->hp[64 * S_THETA + i];
-        double r2 = w->hp[64 * S_TMP + i];
-        rs[i] = sqrt(r2 > 0 ? r2 : 0);
-        key[i] = th[i] * th[i] + rs[i] * rs[i];
-        rz->mu_max = std::max(rz->mu_max, fabs(w->hp[64 * S_RN + i]));
-        rz->theta_dev[i] = th[i];
-        rz->res_dev[i] = rs[i];
-        rz->col[i] = i;
-        if (!isfinite(th[i]) || !isfinite(rs[i])) return QS_ENUMERIC;
-    }
-    std::stable_sort(rz->col, rz->col + k, [&](int a, int b) { return key[a] < key[b]; });
-    for (int i = 0; i < k; ++i) {
-        rz->theta[i] = th[rz->col[i]];
-        rz->res[i] = rs[rz->col[i]];
-    }
-    return QS_OK;
+    return finish_ritz(w, k, rz);
 }
 
 // Chebyshev filter of degree d on Q^2 over [a, b] with FP32 arithmetic: blk32[0] (in)
@@ -245,6 +260,58 @@ static int rayleigh_ritz(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *
 // O(1)).  Each degree is two operator launches: T = Q Y, then the second one computes
 // Y_new = s1 (Q T - c Y) - s2 Y_old in its epilogue.  storage: QS_D32_F32_TILED, or a
 // 16-bit storage whose vectors (52 B per site) live in the same FP32 blocks.
+// ---- the filter stage on FP32 blocks ---------------------------------------------
+// While the block is far from converged (relative residuals above ~1e-3) the basis, its
+// image under Q, the Gram matrices and the rotations stay in FP32 (f32b): no FP64
+// traffic and no FP64 <-> FP32 conversions, which run on GB300's slow FP64 pipe.
+static float *V32(Workspace *w) { return w->f32b[w->iv]; }
+static float *QV32(Workspace *w) { return w->f32b[w->iq]; }
+static float *T32(Workspace *w) { return w->f32b[w->it3]; }
+
+// copy k columns (vectors of nr reals of `bytes` each) src[sel[i]] -> dst[i]
+static int gather_raw(qs_lattice *lat, const void *src, const int *sel, int h, void *dst, size_t vbytes)
+{
+    for (int i = 0; i < h; ++i)
+        CK(cudaMemcpyAsync((char *)dst + (size_t)i * vbytes, (const char *)src + (size_t)sel[i] * vbytes, vbytes,
+                           cudaMemcpyDeviceToDevice, lat->stream));
+    return QS_OK;
+}
+
+static int orthonormalize32(qs_lattice *lat, Workspace *w, int k)
+{
+    cudaStream_t st = lat->stream;
+    CK(qs_norm2<float>(V32(w), k, w->nr, w->part, DS(w, S_TMP), st));
+    CK(qs_map_scalars(DS(w, S_TMP), DS(w, S_COEF), k, 0, st));
+    CK(qs_scale_cols<float>(V32(w), DS(w, S_COEF), k, w->nr, st));
+    for (int pass = 0; pass < 2; ++pass) {
+        CK(qs_gram32(V32(w), k, V32(w), k, w->nr, w->part, w->G, st));
+        CK(qs_chol_rinv(w->G, k, w->Rinv, w->di + 64 + pass, st));
+        CK(qs_rotate32(V32(w), k, w->Rinv, k, w->nr, T32(w), st));
+        std::swap(w->iv, w->it3);
+    }
+    return QS_OK;
+}
+
+// the Rayleigh-Ritz of rayleigh_ritz() with the FP32 operator on the FP32 basis
+static int rayleigh_ritz32(qs_lattice *lat, Workspace *w, double m0, int k, Ritz *rz)
+{
+    cudaStream_t st = lat->stream;
+    QS_TRY(opQ(lat, w, QS_F32, m0, V32(w), QV32(w), k));
+    CK(qs_gram32(QV32(w), k, QV32(w), k, w->nr, w->part, w->Hm, st));
+    CK(qs_herm_eig(w->Hm, k, DS(w, S_RN), w->Ym, w->di + 66, st));
+    CK(qs_gram32(V32(w), k, QV32(w), k, w->nr, w->part, w->Hm, st));
+    CK(qs_herm_eig(w->Hm, k, DS(w, S_THETA), w->Ym, w->di + 67, st));
+    CK(qs_rotate32(V32(w), k, w->Ym, k, w->nr, T32(w), st));
+    std::swap(w->iv, w->it3);
+    CK(qs_rotate32(QV32(w), k, w->Ym, k, w->nr, T32(w), st));
+    std::swap(w->iq, w->it3);
+    CK(qs_resid2<float>(QV32(w), V32(w), DS(w, S_THETA), k, w->nr, w->part, DS(w, S_TMP), st));
+    CK(cudaMemcpyAsync(w->hp + 64 * S_THETA, DS(w, S_THETA), k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w->hp + 64 * S_RN, DS(w, S_RN), k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QS_TRY(sync_read(lat, w, S_TMP, k));
+    return finish_ritz(w, k, rz);
+}
+
 // the launches of one filter, in order: step i (0-based) is T = Q Y_i, then
 // Y_{i+1} = s1_i (Q T - c Y_i) - s2_i Y_{i-1}; returns the result buffer.  With coef_dev the
 // coefficients of step i and the masses are read from the device tables.
@@ -445,21 +512,22 @@ static int solve_q2_mixed(qs_lattice *lat, Workspace *w, double m0, int k, const
 }
 
 // k / 2 representatives of the block V = blk64[0] (device columns, written to sel)
-// whose span together with their C* partners P v is the span of V.  Candidates are
-// taken in Ritz order (rz->col).  If the span is known to be closed under P, M = V^H P V
-// (FP32 products) gives the coordinates of every partner, and a candidate is kept only
-// if it has a component of norm^2 > 1/2 outside span{v_s, P v_s} of those kept so far
-// (Gram-Schmidt in the k coordinates), so nearly degenerate pairs cannot both be picked.
-static int pick_representatives(qs_lattice *lat, Workspace *w, const Ritz *rz, int k, int *sel)
+// whose span together with their C* partners P v is (as nearly as possible) the span of
+// V.  Candidates are taken in Ritz order (rz->col).  M = V^H P V (FP32 products) gives the
+// coordinates in V of the projection of every partner; a candidate is kept only if it has
+// a component of norm^2 > 1/2 outside span{v_s, P v_s} of those kept so far (Gram-Schmidt
+// in the k coordinates), so the two members of a degenerate pair are never both picked.
+static int pick_representatives(qs_lattice *lat, Workspace *w, const Ritz *rz, int k, int *sel, bool fp32)
 {
     const int h = k / 2;
-    if (!w->pinv) {
-        for (int i = 0; i < h; ++i) sel[i] = rz->col[i];
-        return QS_OK;
-    }
     cudaStream_t st = lat->stream;
-    CK(qs_partner(w->blk64[0], w->blk64[3], lat->g, k, 1, st));
-    CK(qs_gram(w->blk64[0], k, w->blk64[3], k, w->nr, w->part, w->G, st, 1));
+    if (fp32) {
+        CK(qs_partner32(V32(w), T32(w), lat->g, k, st));
+        CK(qs_gram32(V32(w), k, T32(w), k, w->nr, w->part, w->G, st));
+    } else {
+        CK(qs_partner(w->blk64[0], w->blk64[3], lat->g, k, 1, st));
+        CK(qs_gram(w->blk64[0], k, w->blk64[3], k, w->nr, w->part, w->G, st, 1));
+    }
     static thread_local double2 M[64 * 64];
     CK(cudaMemcpyAsync(M, w->G, (size_t)k * k * sizeof(double2), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -505,7 +573,7 @@ static int pick_representatives(qs_lattice *lat, Workspace *w, const Ritz *rz, i
             basis.push_back(rm);
         }
     }
-    for (int i = 0; i < k && n < h; ++i)   // not expected for a closed span
+    for (int i = 0; i < k && n < h; ++i)   // only if the span is far from closed under P
         if (!used[rz->col[i]]) { sel[n++] = rz->col[i]; used[rz->col[i]] = true; }
     return QS_OK;
 }
@@ -566,8 +634,29 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
     // allows it (with the FP64 operator their rounding is ~1e-7 relative to the
     // eigenvalue scale); rotations stay FP64 there
     const int glow = (!plain && o->tol >= 1e-6) ? 1 : 0;
-    QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : 1, plain ? 0 : 1));
-    QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, plain ? QS_F64 : QS_F32, plain ? 0 : 1));
+    // in32: the current basis is the FP32 one (filter stage of the mixed forms); else blk64[0]
+    bool in32 = false;
+    auto to32 = [&]() -> int {          // FP64 basis -> FP32 basis
+        CK(qs_d2f(w->blk64[0], V32(w), nullptr, k, w->nr, st));
+        in32 = true;
+        return QS_OK;
+    };
+    auto to64 = [&]() -> int {          // FP32 basis -> FP64 basis
+        if (in32) CK(qs_f2d(V32(w), w->blk64[0], k, w->nr, st));
+        in32 = false;
+        return QS_OK;
+    };
+    auto rr32 = [&]() -> int {          // FP32 orthonormalisation + Rayleigh-Ritz
+        QS_TRY(orthonormalize32(lat, w, k));
+        return rayleigh_ritz32(lat, w, m0, k, rz);
+    };
+    if (plain) {
+        QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, 0, 0));
+        QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F64, 0));
+    } else {
+        QS_TRY(to32());
+        QS_TRY(rr32());
+    }
     // b >= lambda_max(Q^2): ||Q|| = ||D|| <= max_x ||4 + m0 + A(x)|| + ||hopping||,
     // ||hopping|| <= 4 (each direction is a partial isometry pair of norm 1)
     double qn = fabs(4.0 + m0) + lat->clov_norm + 4.0;
@@ -596,6 +685,7 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             // both stages stagnate (typically a warm start from a distant mass): keep the
             // converged pairs, moved to the front so Cholesky-QR preserves them, and
             // refill the rest of the block with random vectors
+            QS_TRY(to64());
             int nconv = 0;
             double2 P[64 * 64];
             for (int i = 0; i < k * k; ++i) P[i] = make_double2(0, 0);
@@ -609,8 +699,13 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             CK(qs_fill_gauss(w->blk64[0] + (size_t)nconv * w->nr, (int64_t)(k - nconv) * w->nr,
                              o->seed * 0x2545F4914F6CDD1DULL + 977 * (restarts + 1), st));
             w->pinv = 0;
-            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : 1, plain ? 0 : 1));
-            QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, plain ? QS_F64 : QS_F32, plain ? 0 : 1));
+            if (plain) {
+                QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, 0, 0));
+                QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F64, 0));
+            } else {
+                QS_TRY(to32());
+                QS_TRY(rr32());
+            }
             last_prec = plain ? QS_F64 : QS_F32;
             stall = fstall = 0;
             prev_worst = 1e300;
@@ -625,11 +720,13 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         if (worst <= o->tol) {
             if (last_prec == QS_F64) { *conv = 1; break; }
             // confirm with the FP64 operator (and an FP64-orthonormal block) before accepting
+            QS_TRY(to64());
             QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, glow, 0));
             QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, QS_F64, glow));
             last_prec = QS_F64;
             continue;
         }
+        bool paired = false;
         if (!refine) {
             // Chebyshev filter on [a, b], a = largest Q^2 Ritz value of the block
             double a = rz->mu_max;
@@ -637,34 +734,44 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             if (plain) {
                 QS_TRY(cheb_filter64(lat, w, m0, k, std::max(2, o->cheb_degree), a, b));
             } else {
+                if (!in32) QS_TRY(to32());
                 const int storage = o->precision == QS_F16 ? QS_D32_F16
                                   : o->precision == QS_BF16 ? QS_D32_BF16 : QS_D32_F32_TILED;
                 // C* pairing: filter k / 2 representatives, their partners complete the
                 // block (the filter is a polynomial in Q^2, which commutes with P)
-                const int kf = pair ? k / 2 : k;
-                const double *src = w->blk64[0];
-                if (pair) {
+                // (a random start block is first filtered whole: its Ritz vectors are not yet
+                // close to pairs)
+                const bool pp = pair && (w->pinv || nf + nref > 0);
+                const int kf = pp ? k / 2 : k;
+                const size_t vb32 = w->nr * sizeof(float);
+                const float *src = V32(w);
+                if (pp) {
                     int sel[32];
-                    QS_TRY(pick_representatives(lat, w, rz, k, sel));
-                    QS_TRY(gather_columns(lat, w, sel, kf, w->blk64[2], nullptr));
-                    src = w->blk64[2];
+                    QS_TRY(pick_representatives(lat, w, rz, k, sel, true));
+                    QS_TRY(gather_raw(lat, V32(w), sel, kf, T32(w), vb32));
+                    src = T32(w);
                 }
-                if (storage == QS_D32_F32_TILED) CK(qs_d2f(src, w->blk32[0], nullptr, kf, w->nr, st));
-                else CK(qs_q16_from_f64(storage, src, w->blk32[0], lat->g.Ns, kf, st));
+                if (storage == QS_D32_F32_TILED)
+                    CK(cudaMemcpyAsync(w->blk32[0], src, kf * vb32, cudaMemcpyDeviceToDevice, st));
+                else
+                    CK(qs_convert_tiled(QS_D32_F32_TILED, storage, src, w->blk32[0], lat->g.Ns, kf, st));
                 void *Y = nullptr;
                 QS_TRY(cheb_filter(lat, w, m0, kf, std::max(2, o->cheb_degree), a, b, storage, &Y));
-                if (storage == QS_D32_F32_TILED) CK(qs_f2d((const float *)Y, w->blk64[2], kf, w->nr, st));
-                else CK(qs_f64_from_q16(storage, Y, w->blk64[2], lat->g.Ns, kf, st));
-                if (pair) {
-                    CK(qs_partner(w->blk64[2], w->blk64[2] + (size_t)kf * w->nr, lat->g, kf, 1, st));
+                if (storage == QS_D32_F32_TILED)
+                    CK(cudaMemcpyAsync(V32(w), Y, kf * vb32, cudaMemcpyDeviceToDevice, st));
+                else
+                    CK(qs_convert_tiled(storage, QS_D32_F32_TILED, Y, V32(w), lat->g.Ns, kf, st));
+                if (pp) {
+                    CK(qs_partner32(V32(w), V32(w) + (size_t)kf * w->nr, lat->g, kf, st));
                     w->pinv = 1;
+                    paired = true;
                 }
-                std::swap(w->blk64[0], w->blk64[2]);
             }
             ++nf;
         } else {
             // power step with Q^-2: X = Q^-2 V, started from V_i / <v_i, Q^2 v_i>
             // (<v, Q^2 v> = theta^2 + r^2 for each Ritz vector)
+            QS_TRY(to64());
             double inv[64];
             for (int i = 0; i < k; ++i) {   // device column order
                 double q2 = rz->theta_dev[i] * rz->theta_dev[i] + rz->res_dev[i] * rz->res_dev[i];
@@ -672,17 +779,18 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
             }
             // solve accuracy tied to the absolute residual the target needs
             double tsol = std::max(1e-13, std::min(1e-2, 0.05 * worst * fabs(rz->theta[0])));
-            if (pair) {
+            if (pair && (w->pinv || nf + nref > 0)) {
                 // Q^-2 commutes with P: solve for k / 2 representatives, partners complete
                 const int h = k / 2;
                 int sel[32];
-                QS_TRY(pick_representatives(lat, w, rz, k, sel));
+                QS_TRY(pick_representatives(lat, w, rz, k, sel, false));
                 QS_TRY(gather_columns(lat, w, sel, h, w->blk64[3], nullptr));
                 QS_TRY(gather_columns(lat, w, sel, h, w->blk64[2], inv));
                 int s = solve_q2_mixed(lat, w, m0, h, w->blk64[3], w->blk64[2], w->blk64[4], w->blk64[5], tsol);
                 if (s != QS_OK && s != QS_ENOCONV) return s;
                 CK(qs_partner(w->blk64[2], w->blk64[2] + (size_t)h * w->nr, lat->g, h, 1, st));
                 w->pinv = 1;
+                paired = true;
             } else {
                 CK(cudaMemcpyAsync(DS(w, S_COEF), inv, k * sizeof(double), cudaMemcpyHostToDevice, st));
                 CK(qs_scaled_copy(w->blk64[2], w->blk64[0], DS(w, S_COEF), k, w->nr, st));
@@ -695,15 +803,39 @@ int qs_lowmodes_impl(qs_lattice *lat, double m0, const qs_eig_opts *o, Ritz *rz,
         // FP32 operator, Gram and rotation while the block is far from converged (its
         // residuals are then far above FP32 rounding); FP64 from the refinement on
         last_prec = (plain || refine || worst < 1e-3) ? QS_F64 : QS_F32;
-        const int f32 = last_prec == QS_F32;
-        QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, f32 || glow, f32));
-        QS_TRY(rayleigh_ritz(lat, w, m0, k, rz, last_prec, glow));
+        int rr;
+        if (last_prec == QS_F32) {
+            if (!in32) QS_TRY(to32());
+            rr = rr32();
+        } else {
+            QS_TRY(to64());
+            QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, plain ? 0 : glow, 0));
+            rr = rayleigh_ritz(lat, w, m0, k, rz, QS_F64, plain ? 0 : glow);
+        }
+        if (rr == QS_ENUMERIC && paired) {
+            // the completed block was (numerically) rank deficient: replace the partner half
+            // by random vectors and orthonormalise again
+            QS_TRY(to64());
+            CK(qs_fill_gauss(w->blk64[0] + (size_t)(k / 2) * w->nr, (int64_t)(k - k / 2) * w->nr,
+                             o->seed * 0x5851F42D4C957F2DULL + 31 * (it + 1), st));
+            w->pinv = 0;
+            CK(cudaMemsetAsync(w->di + 64, 0, 2 * sizeof(int), st));
+            if (last_prec == QS_F32) {
+                QS_TRY(to32());
+                rr = rr32();
+            } else {
+                QS_TRY(orthonormalize(lat, w, w->blk64[0], w->blk64[2], k, glow, 0));
+                rr = rayleigh_ritz(lat, w, m0, k, rz, QS_F64, glow);
+            }
+        }
+        QS_TRY(rr);
         double nw = 0;
         for (int i = 0; i < o->nwant; ++i) nw = std::max(nw, rel(i));
         if (refine) { if (nw > 0.97 * prev_worst) ++stall; else stall = 0; }
         else { if (nw > 0.9 * prev_worst) ++fstall; else fstall = 0; }
         prev_worst = nw;
     }
+    QS_TRY(to64());   // the FP64 block is the result (and the next warm start)
     w->have_V = 1;
     if (stats) {
         stats->iterations = it;

@@ -80,7 +80,7 @@ def run_study(train_L=8, train_T=16, flows=200, eval_L=16, eval_T=32, eval_confi
     from synth_inputs import kappa_to_m0, make_config, mlp_init
 
     field = dict(eps=0.2, theta_sigma=0.3, csw_su3=1.9, csw_u1=1.0)
-    opts = qs.sign_default_opts(eig={"k": 24, "nwant": 2, "tol": 1e-5, "cheb_degree": 32, "precision": 2})
+    opts = qs.sign_default_opts(eig={"k": 32, "nwant": 2, "tol": 1e-5, "cheb_degree": 48, "precision": 2})
     stream = torch.cuda.Stream()
     Xs, Ts, t0 = [], [], time.perf_counter()
     for i in range(flows):
@@ -93,7 +93,7 @@ def run_study(train_L=8, train_T=16, flows=200, eval_L=16, eval_T=32, eval_confi
             Xs.append(X)
             Ts.append(T)
         except qs.QStarError as e:
-            log(f"[learned] training flow {i}: {e}")
+            log(f"[learned] training flow {i}: {e} (fail_reason {getattr(e, 'report', {}).get('fail_reason')})")
         lat.close()
     X, T = np.concatenate(Xs), np.concatenate(Ts)
     t_gen = time.perf_counter() - t0
@@ -114,23 +114,29 @@ def run_study(train_L=8, train_T=16, flows=200, eval_L=16, eval_T=32, eval_confi
         for name, model in (("plain", None), ("learned", net)):
             stream.synchronize()
             t1 = time.perf_counter()
-            s, rep = lat.pfaffian_sign(m, opts, step_model=model)
+            try:
+                s, rep = lat.pfaffian_sign(m, opts, step_model=model)
+                res[name] = {"sign": s, "masses": rep["n"], "s": time.perf_counter() - t1,
+                             "accepted": rep["learned_accepted"], "rejected": rep["learned_rejected"]}
+            except qs.QStarError as e:
+                rep = getattr(e, "report", {})
+                res[name] = {"error": str(e), "fail_reason": rep.get("fail_reason"), "masses": rep.get("n"),
+                             "s": time.perf_counter() - t1}
             stream.synchronize()
-            res[name] = {"sign": s, "masses": rep["n"], "s": time.perf_counter() - t1,
-                         "accepted": rep["learned_accepted"], "rejected": rep["learned_rejected"]}
         rows.append(res)
         log(f"[learned] eval {j}: {res}")
         lat.close()
-    plain_n = sum(r["plain"]["masses"] for r in rows)
-    learned_n = sum(r["learned"]["masses"] for r in rows)
+    ok = [r for r in rows if "sign" in r["plain"] and "sign" in r["learned"]]
+    plain_n = sum(r["plain"]["masses"] for r in ok)
+    learned_n = sum(r["learned"]["masses"] for r in ok)
     out_d = {"train": {"lattice": f"{train_L}^3x{train_T}", "flows": flows, "samples": int(len(X)),
                        "kappas": list(kappas), "s_flows": t_gen, "s_train": t_train,
                        "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "adam_steps": steps},
              "eval": {"lattice": f"{eval_L}^3x{eval_T}", "configs": eval_configs, "rows": rows,
-                      "masses_plain": plain_n, "masses_learned": learned_n,
-                      "s_plain": sum(r["plain"]["s"] for r in rows),
-                      "s_learned": sum(r["learned"]["s"] for r in rows),
-                      "signs_identical": all(r["plain"]["sign"] == r["learned"]["sign"] for r in rows)}}
+                      "completed_both": len(ok), "masses_plain": plain_n, "masses_learned": learned_n,
+                      "s_plain": sum(r["plain"]["s"] for r in ok),
+                      "s_learned": sum(r["learned"]["s"] for r in ok),
+                      "signs_identical": all(r["plain"]["sign"] == r["learned"]["sign"] for r in ok)}}
     net.close()
     if out:
         import json
