@@ -330,7 +330,7 @@ def big_extras(qs, args, peak):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         eo = qs.eig_default_opts(k=k, nwant=4, tol=1e-8, cheb_degree=args.degree, warm_start=0,
-                                 max_iter=60, precision=2)
+                                 max_iter=40, precision=2)
         ev, rs, st = lat.lowmodes_at_mass(m0, eo, allow_noconv=True)
         torch.cuda.synchronize()
         t_mixed = time.perf_counter() - t1

@@ -292,6 +292,15 @@ typedef struct {
                           the negative count; 5 max_steps reached; 6 lambda_bar - r <= 0 */
 } qs_sign_report;
 
+/* The bounds step A takes from one block of Ritz pairs (host arithmetic, no GPU work):
+ * *lambda_bar = min |theta_j| and *lo = min (|theta_j| - res_j) over the values that carry
+ * information: the first nwant (the converged ones) and every other one with
+ * res_j <= |theta_j| / 2 (k <= 64).  The block is ordered by theta^2 + res^2, so the smallest lower
+ * bound need not be the first value's.  theta, res: HOST arrays of k values.  Sec. 3 (the
+ * derivative bound: no eigenvalue of Q crosses zero within lo of the mass). */
+QS_API int qs_block_bounds(const double *theta, const double *res, int k, int nwant, double *lambda_bar,
+                           double *lo);
+
 /* Fill *opts with defaults (c = 1.9, m0_max = 0 (auto), max_steps = 400, eig defaults
  * with tol = 1e-5).  Step A also stops as soon as m + (lambda_bar - r) > m0_max. */
 QS_API void qs_sign_default_opts(qs_sign_opts *opts);
@@ -318,6 +327,16 @@ QS_API int qs_log_det_oo(qs_lattice *lat, int nmass, const double *m0, double *l
 
 /* *w_eo = W_eo(m -> mp) and *log_w_eo its logarithm (either may be NULL, not both). */
 QS_API int qs_w_eo(qs_lattice *lat, double m, double mp, double *w_eo, double *log_w_eo);
+
+/* The even-odd preconditioned operator of Sec. 4: out = D_hat(m0) in, with
+ * D_hat = D_ee - D_eo (D_oo)^-1 D_oe on the even sites (gamma5 = 1: Q_hat = gamma_5 D_hat).
+ * in, out: DEVICE buffers of nrhs <= 64 FP64 spinors in the canonical layout of the full
+ * doubled lattice; the odd-site entries of in are ignored and those of out set to zero.
+ * FP64 arithmetic (two operator applications and a site-local 6 x 6 solve per odd site);
+ * allocates three work vectors per call; synchronises the stream.  QS_EINVAL for an odd T
+ * or L (then a hop can join two sites of one parity), overlapping or unaligned buffers.  det D = det D_oo det D_hat,
+ * which is why W_eo carries the D_oo part of a mass reweighting. */
+QS_API int qs_apply_Dhat(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int gamma5);
 
 /* W_sgn for n configurations at once (the batched form; Sec. 3 runs the algorithm on
  * each configuration independently).  lats: n distinct handles with gauge fields

@@ -9,12 +9,14 @@ site-diagonal part 4 + m0 + A(x) there, and
   W_eo(m -> m') = |det[D^oo_m' (D^oo_m)^-1]|^(1/2) = exp((log|det D^oo_m'| - log|det D^oo_m|) / 2).
 
 ``log_det_oo`` evaluates the definition block by block (numpy slogdet of each 12 x 12
-block); ``schur_det`` forms det D = det D^oo det(D^ee - D^eo (D^oo)^-1 D^oe) densely.
+block); ``dhat_dense`` forms the preconditioned operator D_hat = D^ee - D^eo (D^oo)^-1 D^oe
+from the dense D, and ``schur_det`` the identity det D = det D^oo det D_hat.
 
 Pins (tests/test_oracle_evenodd.py): the odd-odd part of the dense D has no entries
 between different sites; the dense slogdet of that part equals ``log_det_oo``; the
 Schur identity det D = det D^oo det D_hat holds on a rough field; the free field gives
-the closed form log|det D^oo| = 12 N_odd log|4 + m0|.
+the closed form log|det D^oo| = 12 N_odd log|4 + m0|; on the free field D_hat x equals
+(4 + m0) x - H^2 x / (4 + m0) with H the hopping part, applied by the matrix-free operator.
 """
 import numpy as np
 
@@ -41,12 +43,23 @@ def w_eo(op, m, mp):
     return float(np.exp(0.5 * (log_det_oo(op, mp) - log_det_oo(op, m))))
 
 
-def schur_det(op, m0):
-    """(log|det D^oo|, log|det D_hat|, log|det D|) from the dense D, D_hat the Schur
-    complement D^ee - D^eo (D^oo)^-1 D^oe on the even sites."""
+def dhat_dense(op, m0, gamma5=False):
+    """(D_hat, e): the Schur complement D^ee - D^eo (D^oo)^-1 D^oe of the dense D on the
+    even sites (gamma_5 D_hat if asked), and the indices e of the even-site components
+    in the flat canonical vector, in the order D_hat's rows use."""
     D = op.dense_D(m0)
     p = np.repeat(parity(op.lat), 12)
     e, o = np.nonzero(p == 0)[0], np.nonzero(p == 1)[0]
-    Doo = D[np.ix_(o, o)]
-    Dhat = D[np.ix_(e, e)] - D[np.ix_(e, o)] @ np.linalg.solve(Doo, D[np.ix_(o, e)])
-    return (np.linalg.slogdet(Doo)[1], np.linalg.slogdet(Dhat)[1], np.linalg.slogdet(D)[1])
+    Dhat = D[np.ix_(e, e)] - D[np.ix_(e, o)] @ np.linalg.solve(D[np.ix_(o, o)], D[np.ix_(o, e)])
+    if gamma5:
+        g5 = np.where(np.arange(D.shape[0]) % 12 >= 6, -1.0, 1.0)[e]   # chiral basis: spins 2, 3
+        Dhat = g5[:, None] * Dhat
+    return Dhat, e
+
+
+def schur_det(op, m0):
+    """(log|det D^oo|, log|det D_hat|, log|det D|) from the dense D."""
+    D = op.dense_D(m0)
+    o = np.nonzero(np.repeat(parity(op.lat), 12) == 1)[0]
+    Dhat, _ = dhat_dense(op, m0)
+    return (np.linalg.slogdet(D[np.ix_(o, o)])[1], np.linalg.slogdet(Dhat)[1], np.linalg.slogdet(D)[1])

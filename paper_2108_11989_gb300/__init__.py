@@ -128,6 +128,8 @@ def _load():
         "qs_log_det_oo": (I, [P, I, P, P]),
         "qs_cstar_partner": (I, [P, P, P, I, I]),
         "qs_w_eo": (I, [P, D, D, P, P]),
+        "qs_apply_Dhat": (I, [P, D, P, P, I, I]),
+        "qs_block_bounds": (I, [P, P, I, I, P, P]),
         "qs_apply_Q_norm2_noalloc": (I, [P, D, P, P, I, I, P]),
         "qs_strerror": (ctypes.c_char_p, [I]),
         "qs_last_cuda_error": (ctypes.c_char_p, []),
@@ -301,6 +303,27 @@ def log_det_oo(h, masses):
     return out
 
 
+def block_bounds(theta, res, nwant):
+    """qs_block_bounds: (lambda_bar, lo) step A takes from a block of Ritz pairs."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    rs = np.ascontiguousarray(res, dtype=np.float64)
+    if th.shape != rs.shape or th.ndim != 1:
+        raise ValueError("theta and res must be 1-D arrays of one length")
+    lb, lo = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.qs_block_bounds(th.ctypes.data, rs.ctypes.data, th.size, int(nwant), ctypes.byref(lb),
+                                ctypes.byref(lo)), "block_bounds")
+    return lb.value, lo.value
+
+
+def apply_Dhat(h, m0, inp, out, gamma5=False):
+    """qs_apply_Dhat: even-odd preconditioned D_hat (or Q_hat) on float64 device spinors."""
+    import torch
+    if inp.dtype != torch.float64 or out.dtype != torch.float64 or inp.shape != out.shape:
+        raise TypeError("apply_Dhat takes two float64 spinor tensors of one shape")
+    _check(_lib.qs_apply_Dhat(h, float(m0), inp.data_ptr(), out.data_ptr(), _nrhs(h, inp), int(bool(gamma5))),
+           "apply_Dhat")
+
+
 def w_eo(h, m, mp):
     """qs_w_eo: (W_eo(m -> m'), log W_eo)."""
     w, lw = ctypes.c_double(0), ctypes.c_double(0)
@@ -470,6 +493,9 @@ class Lattice:
 
     def apply_Q(self, m0, inp, out, tiled=False, prec=None):
         apply_Q(self.h, m0, inp, out, tiled, prec)
+
+    def apply_Dhat(self, m0, inp, out, gamma5=False):
+        apply_Dhat(self.h, m0, inp, out, gamma5)
 
     def lowmodes_at_mass(self, m0, opts=None, evecs=None, allow_noconv=False):
         return lowmodes_at_mass(self.h, m0, opts, evecs, allow_noconv)

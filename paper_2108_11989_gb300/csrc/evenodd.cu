@@ -139,3 +139,172 @@ extern "C" int qs_w_eo(qs_lattice *lat, double m, double mp, double *w_eo, doubl
     if (w_eo) *w_eo = exp(lw);
     return QS_OK;
 }
+
+// ---- the even-odd preconditioned operator (Sec. 4) --------------------------------
+// D_hat = D_ee - D_eo (D_oo)^-1 D_oe on the even sites, Q_hat = gamma_5 D_hat.  With x the
+// even part of the input (odd entries zero): (D x)_e = D_ee x_e and (D x)_o = D_oe x_e, so
+//   D_hat x_e = (D x)_e - (D u)_e,  u = (D_oo)^-1 (D x)_o  (u zero on even sites),
+// two applications of the full FP64 operator, a site-local solve and parity masks.
+namespace {
+
+__device__ __forceinline__ int site_parity(const Geom &g, int64_t s)
+{
+    const int x = (int)(s % g.L2);
+    int64_t r = s / g.L2;
+    const int y = (int)(r % g.L);
+    r /= g.L;
+    const int z = (int)(r % g.L);
+    const int t = (int)(r / g.L);
+    return (t + z + y + x) & 1;
+}
+
+// out = in on sites of parity `keep`, 0 elsewhere (canonical FP64 layout, k vectors)
+__global__ void parity_mask_kernel(const double2 *__restrict__ in, double2 *__restrict__ out, Geom g, int k,
+                                   int keep)
+{
+    const int64_t n = g.Ns * 12 * k;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t s = (i / 12) % g.Ns;
+    out[i] = site_parity(g, s) == keep ? in[i] : make_double2(0, 0);
+}
+
+// out_e = a_e - b_e (gamma_5 applied if asked), 0 on odd sites
+__global__ void even_diff_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b,
+                                 double2 *__restrict__ out, Geom g, int k, int gamma5)
+{
+    const int64_t n = g.Ns * 12 * k;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t s = (i / 12) % g.Ns;
+    const int comp = (int)(i % 12);
+    if (site_parity(g, s) != 0) { out[i] = make_double2(0, 0); return; }
+    double2 v = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
+    if (gamma5 && comp >= 6) v = make_double2(-v.x, -v.y);
+    out[i] = v;
+}
+
+// u = (4 + m0 + A(x))^-1 t on odd sites (two 6 x 6 chiral blocks, complex Gaussian
+// elimination with partial pivoting in FP64), 0 on even sites; one thread per (vector, site).
+// The mirror site's block is S conj(A) S: entry (i, j) = sign * conj(A[i +- 3][j +- 3]),
+// sign = -1 across the two spin halves.
+__global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const double2 *__restrict__ t,
+                                        double2 *__restrict__ u, Geom g, int k, double dm)
+{
+    const int64_t n = g.Ns * k;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t s = i % g.Ns;
+    const double2 *ti = t + i * 12;
+    double2 *ui = u + i * 12;
+    if (site_parity(g, s) == 0) {
+        for (int c = 0; c < 12; ++c) ui[c] = make_double2(0, 0);
+        return;
+    }
+    const int x = (int)(s % g.L2);
+    const bool mir = x >= g.L;
+    const int64_t p = (s / g.L2) * g.L + (mir ? x - g.L : x);
+    const int64_t V = g.Vphys;
+    for (int b = 0; b < 2; ++b) {
+        const double *cb = clov + (int64_t)b * 36 * V + p;
+        double ar[6][6], ai[6][6], rr[6], ri[6];
+        for (int r = 0; r < 6; ++r)
+            for (int c = 0; c < 6; ++c) {
+                const int ii = mir ? (r + 3) % 6 : r, jj = mir ? (c + 3) % 6 : c;
+                double er, ei;
+                if (ii == jj) { er = cb[(int64_t)ii * V]; ei = 0; }
+                else if (ii > jj) {
+                    const int kk = 6 + 2 * qs_tri(ii, jj);
+                    er = cb[(int64_t)kk * V]; ei = cb[(int64_t)(kk + 1) * V];
+                } else {
+                    const int kk = 6 + 2 * qs_tri(jj, ii);
+                    er = cb[(int64_t)kk * V]; ei = -cb[(int64_t)(kk + 1) * V];
+                }
+                if (mir) {
+                    ei = -ei;
+                    if ((r < 3) != (c < 3)) { er = -er; ei = -ei; }
+                }
+                ar[r][c] = er + (r == c ? dm : 0.0);
+                ai[r][c] = ei;
+            }
+        for (int r = 0; r < 6; ++r) { rr[r] = ti[6 * b + r].x; ri[r] = ti[6 * b + r].y; }
+        for (int c = 0; c < 6; ++c) {
+            int piv = c;
+            double best = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
+            for (int r = c + 1; r < 6; ++r) {
+                const double a2 = ar[r][c] * ar[r][c] + ai[r][c] * ai[r][c];
+                if (a2 > best) { best = a2; piv = r; }
+            }
+            if (piv != c) {
+                for (int j = 0; j < 6; ++j) {
+                    double tt = ar[c][j]; ar[c][j] = ar[piv][j]; ar[piv][j] = tt;
+                    tt = ai[c][j]; ai[c][j] = ai[piv][j]; ai[piv][j] = tt;
+                }
+                double tt = rr[c]; rr[c] = rr[piv]; rr[piv] = tt;
+                tt = ri[c]; ri[c] = ri[piv]; ri[piv] = tt;
+            }
+            const double ir = ar[c][c] / best, ii2 = -ai[c][c] / best;   // 1 / pivot
+            for (int r = c + 1; r < 6; ++r) {
+                const double lr = ar[r][c] * ir - ai[r][c] * ii2, li = ar[r][c] * ii2 + ai[r][c] * ir;
+                for (int j = c; j < 6; ++j) {
+                    ar[r][j] -= lr * ar[c][j] - li * ai[c][j];
+                    ai[r][j] -= lr * ai[c][j] + li * ar[c][j];
+                }
+                rr[r] -= lr * rr[c] - li * ri[c];
+                ri[r] -= lr * ri[c] + li * rr[c];
+            }
+        }
+        for (int r = 5; r >= 0; --r) {   // back substitution
+            double sr = rr[r], si = ri[r];
+            for (int j = r + 1; j < 6; ++j) {
+                sr -= ar[r][j] * rr[j] - ai[r][j] * ri[j];
+                si -= ar[r][j] * ri[j] + ai[r][j] * rr[j];
+            }
+            const double d2 = ar[r][r] * ar[r][r] + ai[r][r] * ai[r][r];
+            rr[r] = (sr * ar[r][r] + si * ai[r][r]) / d2;
+            ri[r] = (si * ar[r][r] - sr * ai[r][r]) / d2;
+        }
+        for (int r = 0; r < 6; ++r) ui[6 * b + r] = make_double2(rr[r], ri[r]);
+    }
+}
+
+}  // namespace
+
+extern "C" int qs_apply_Dhat(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int gamma5)
+{
+    if (!lat || !in || !out || nrhs < 1 || nrhs > 64) return QS_EINVAL;
+    if (!lat->gauge_loaded) return QS_EINVAL;
+    const Geom &g = lat->g;
+    if ((g.T | g.L) & 1) return QS_EINVAL;   // hopping must connect opposite parities only
+    const size_t bytes = (size_t)nrhs * g.Ns * 24 * sizeof(double);
+    const char *a = (const char *)in, *b = (const char *)out;
+    if (a < b + bytes && b < a + bytes) return QS_EINVAL;
+    if (((uintptr_t)in | (uintptr_t)out) & 15) return QS_EINVAL;
+    QS_CUDA(cudaSetDevice(lat->device));
+    cudaStream_t st = lat->stream;
+    double *buf = nullptr;
+    QS_CUDA(cudaMalloc(&buf, 3 * bytes));
+    double *x = buf, *dx = buf + bytes / 8, *w = buf + 2 * bytes / 8;
+    double m[64];
+    for (int r = 0; r < nrhs; ++r) m[r] = m0;
+    const int64_t n = g.Ns * 12 * nrhs;
+    const unsigned nb = (unsigned)((n + 255) / 256), nbs = (unsigned)((g.Ns * nrhs + 127) / 128);
+    int s = QS_OK;
+    do {
+        parity_mask_kernel<<<nb, 256, 0, st>>>((const double2 *)in, (double2 *)x, g, nrhs, 0);
+        qs_note_launches(1);
+        if ((s = qs_dslash_run(lat, QS_F64, m, x, dx, nrhs, 0, 0)) != QS_OK) break;         // D x
+        clover_solve_odd_kernel<<<nbs, 128, 0, st>>>(lat->clov64, (const double2 *)dx, (double2 *)x, g, nrhs,
+                                                     4.0 + m0);                                  // u (in x)
+        qs_note_launches(1);
+        if ((s = qs_dslash_run(lat, QS_F64, m, x, w, nrhs, 0, 0)) != QS_OK) break;          // D u
+        even_diff_kernel<<<nb, 256, 0, st>>>((const double2 *)dx, (const double2 *)w, (double2 *)out, g, nrhs,
+                                             gamma5);
+        qs_note_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_apply_Dhat"); s = QS_ECUDA; }
+    } while (0);
+    cudaFree(buf);
+    return s;
+}

@@ -166,6 +166,15 @@ int propose(Flow &f, double lb, double *dm)
 
 }  // namespace
 
+extern "C" int qs_block_bounds(const double *theta, const double *res, int k, int nwant, double *lb, double *lo)
+{
+    if (!theta || !res || !lb || !lo || k < 1 || k > 64) return QS_EINVAL;
+    Ritz rz;
+    for (int j = 0; j < k; ++j) { rz.theta[j] = theta[j]; rz.res[j] = res[j]; }
+    lambda_bar(rz, k, nwant, lb, lo);
+    return QS_OK;
+}
+
 extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_opts *opts, int *sign,
                                 qs_sign_report *report)
 {
@@ -345,16 +354,25 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
                 if (!(guard_low(rz) > a)) guards_above = 0;
                 *ok = above_gap ? guards_above : pre_above;
             };
-            int before, sb, ab, after, sa, aa;
+            int before, sb, ab, after = 0, sa = 0, aa = 0;
             count_below(cur, &before, &sb, &ab);
+            if (sb || !ab) { rep->fail_reason = 3; return finish(QS_ENOCONV); }
             double lb_old, lo_old;
             lambda_bar(cur, kk, nb, &lb_old, &lo_old);
-            m += dm;
-            st = modes(f, m, 'B', &cur);
-            if (st != QS_OK) return finish(st);
-            ++f.steps;
-            count_below(cur, &after, &sa, &aa);
-            if (sb || sa || !ab || !aa) { rep->fail_reason = 3; return finish(QS_ENOCONV); }
+            const double m_prev = m;
+            for (int tries = 0;; ++tries) {
+                m = m_prev + dm;
+                st = modes(f, m, 'B', &cur);
+                if (st != QS_OK) return finish(st);
+                ++f.steps;
+                count_below(cur, &after, &sa, &aa);
+                if (!sa && aa) break;
+                // the count at the new mass is not certified (a value's bounds straddle
+                // a, or the window no longer bounds everything above a).  The gap at
+                // m_prev rules out a crossing of a for every shorter step too: halve it
+                if (tries == 3 || f.steps >= f.o.max_steps) { rep->fail_reason = 3; return finish(QS_ENOCONV); }
+                dm *= 0.5;
+            }
             int d = after - before;
             if (d % 2) { rep->fail_reason = 4; return finish(QS_ENUMERIC); }   // pairs must stay paired
             flips += d / 2;

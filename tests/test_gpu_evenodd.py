@@ -42,3 +42,44 @@ def test_w_eo_free_field(qs):
     w, lw = qs.w_eo(lat.h, -0.3, 0.7)
     assert abs(lw - 6 * n_odd * np.log(4.7 / 3.7)) <= 1e-11 * abs(lw)
     lat.close()
+
+
+@pytest.mark.parametrize("shape,gamma5", [((4, 2, 0b111), False), ((4, 2, 0b111), True), ((4, 4, 0b011), True)])
+def test_apply_dhat_against_dense_schur_complement(qs, shape, gamma5):
+    """D_hat = D_ee - D_eo (D_oo)^-1 D_oe (Sec. 4) on even-site vectors against the oracle's
+    dense Schur complement; FP64 throughout, tolerance 1e-12 relative to the largest entry."""
+    import torch
+    from oracle.evenodd import dhat_dense
+    T, L, mask = shape
+    cfg = make_config(T=T, L=L, eps=0.7, theta_sigma=0.4, csw_su3=1.9, csw_u1=1.0, seed=11, cstar_mask=mask)
+    lat = qs.Lattice(L, T, mask)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    op = WilsonDirac(cfg)
+    m0 = -0.35
+    Dhat, e = dhat_dense(op, m0, gamma5=gamma5)
+    n = op.lat.n_sites * 12
+    rng = np.random.default_rng(4)
+    nrhs = 3
+    x = rng.normal(size=(nrhs, n)) + 1j * rng.normal(size=(nrhs, n))   # odd entries must be ignored
+    xd = torch.from_numpy(np.stack([x.real, x.imag], -1)).to("cuda")
+    yd = torch.full_like(xd, np.nan)
+    lat.apply_Dhat(m0, xd, yd, gamma5=gamma5)
+    y = yd.cpu().numpy()
+    y = y[..., 0] + 1j * y[..., 1]
+    odd = np.setdiff1d(np.arange(n), e)
+    assert np.all(y[:, odd] == 0)
+    ref = x[:, e] @ Dhat.T
+    err = np.max(np.abs(y[:, e] - ref))
+    assert err <= 1e-12 * np.max(np.abs(ref)), err
+    lat.close()
+
+
+def test_apply_dhat_rejects_odd_extent(qs):
+    import torch
+    cfg = make_config(T=5, L=2, eps=0.5, theta_sigma=0.2, csw_su3=1.0, csw_u1=0.0, seed=1)
+    lat = qs.Lattice(2, 5)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    x = torch.zeros(lat.n_sites * 24, dtype=torch.float64, device="cuda")
+    with pytest.raises(qs.QStarError):
+        lat.apply_Dhat(0.0, x, torch.empty_like(x))
+    lat.close()

@@ -36,11 +36,13 @@ def test_learned_steps_keep_signs_and_report_gain():
     losses = train(net, X, T, steps=300, lr=2e-3)
     assert losses[-1] < losses[0]
     plain_n, learned_n, accepted, rejected = 0, 0, 0, 0
+    held_X = []
     for seed in range(100, 104):
         c = cfg(seed)
         lat = qs.Lattice(c.L, c.T)
         lat.load_gauge(c.su3, c.theta, c.csw_su3, c.csw_u1)
-        s0, r0 = lat.pfaffian_sign(m_target, opts)
+        s0, r0 = lat.pfaffian_sign(m_target, opts, trace=True)
+        held_X.append(samples_from_flow(r0)[0])
         s1, r1 = lat.pfaffian_sign(m_target, opts, step_model=net)
         assert s0 == s1
         plain_n += r0["n"]
@@ -49,6 +51,15 @@ def test_learned_steps_keep_signs_and_report_gain():
         rejected += r1["learned_rejected"]
         lat.close()
     assert accepted + rejected > 0
+    # the trained network on held-out windows: the library's forward pass equals the FP64
+    # oracle's forward pass with the same parameters
+    import torch
+    from oracle import mlp as mlp_oracle
+    Xh = np.concatenate(held_X)
+    assert len(Xh) > 0
+    Yg = net.forward(torch.from_numpy(np.ascontiguousarray(Xh, dtype=np.float32)).cuda()).cpu().numpy()
+    Yr, _ = mlp_oracle.forward(net.get_params(), Xh)
+    assert np.abs(Yg - Yr).max() <= 1e-4 * (1.0 + np.abs(Yr).max())
     print(f"\n[learned step] samples={len(X)} loss {losses[0]:.3f}->{losses[-1]:.3f}; mass points "
           f"plain={plain_n} learned={learned_n}; proposals accepted={accepted} rejected={rejected}")
     net.close()

@@ -89,3 +89,33 @@ def test_batched_sign_matches_single_flows(qs):
     assert out[1][0] == -1          # the 4^4 golden mass -2.005 has W_sgn = -1
     for lat in lats:
         lat.close()
+
+
+def test_block_bounds_take_the_smallest_informative_lower_bound(qs):
+    """Step A's bounds (Sec. 3, derivative bound) come from the whole block: the block is
+    ordered by theta^2 + r^2, so the smallest |theta_j| - r_j can belong to a later value."""
+    theta = [0.30, -0.31, 0.05, 0.9]
+    res = [0.01, 0.10, 0.04, 0.5]
+    # value 1 (r <= |theta| / 2) has the smallest lower bound, 0.21, below value 0's 0.29;
+    # value 2 (r > |theta| / 2, beyond nwant) is an unconverged mixture and is skipped
+    lb, lo = qs.block_bounds(theta, res, nwant=1)
+    assert lb == 0.30 and abs(lo - 0.21) < 1e-15
+    # within nwant every value counts, converged or not
+    lb, lo = qs.block_bounds(theta, res, nwant=3)
+    assert lb == 0.05 and abs(lo - 0.01) < 1e-15
+
+
+def test_block_bounds_certify_the_exact_spectrum(qs):
+    """On the rough 2^3x4 field: lo from a solved block lies below the exact smallest
+    |lambda| of Q (dense oracle) and within the eigensolver's tolerance of it."""
+    cfg = make_config(T=4, L=2, eps=2.0, theta_sigma=0.3, csw_su3=1.5, csw_u1=1.0, seed=2)
+    op = WilsonDirac(cfg)
+    lat = lattice(qs, cfg)
+    for m in (-1.85, -1.5):
+        o = qs.eig_default_opts(k=16, nwant=4, tol=1e-8, cheb_degree=16)
+        ev, rs, _ = lat.lowmodes_at_mass(m, o)
+        lb, lo = qs.block_bounds(ev, rs, nwant=4)
+        exact = np.min(np.abs(np.linalg.eigvalsh(op.dense_Q(m))))
+        assert lo <= exact <= lb + 1e-6, (m, lo, exact, lb)
+        assert exact - lo < 1e-6 * max(1.0, exact)
+    lat.close()

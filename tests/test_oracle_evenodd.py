@@ -4,7 +4,7 @@ import pytest
 
 from synth_inputs import GaugeConfig, make_config, unit_su3_field
 from oracle.dirac import WilsonDirac
-from oracle.evenodd import log_det_oo, parity, schur_det, w_eo
+from oracle.evenodd import dhat_dense, log_det_oo, parity, schur_det, w_eo
 
 
 @pytest.fixture(scope="module")
@@ -37,3 +37,24 @@ def test_free_field_closed_form():
     for m0 in (-0.3, 0.7):
         assert np.isclose(log_det_oo(op, m0), 12 * n_odd * np.log(abs(4.0 + m0)), rtol=1e-13)
     assert np.isclose(w_eo(op, -0.3, 0.7), (4.7 / 3.7) ** (6 * n_odd), rtol=1e-12)
+
+
+def test_dhat_inverts_the_full_solve_on_even_sites(rough):
+    # D y = (b_e, 0)  =>  D_hat y_e = b_e  (block elimination of the odd sites)
+    m0 = -0.35
+    Dhat, e = dhat_dense(rough, m0)
+    rng = np.random.default_rng(3)
+    n = rough.dense_D(m0).shape[0]
+    b = np.zeros(n, complex)
+    b[e] = rng.normal(size=e.size) + 1j * rng.normal(size=e.size)
+    y = np.linalg.solve(rough.dense_D(m0), b)
+    assert np.allclose(Dhat @ y[e], b[e], rtol=0, atol=1e-11 * np.abs(b).max())
+    assert np.array_equal(e, np.nonzero(np.repeat(parity(rough.lat), 12) == 0)[0])
+
+
+def test_qhat_is_hermitian(rough):
+    # gamma_5 D is Hermitian, so its Schur complement gamma_5 D_hat is Hermitian too
+    Qhat, _ = dhat_dense(rough, 0.1, gamma5=True)
+    Dhat, _ = dhat_dense(rough, 0.1)
+    assert np.max(np.abs(Qhat - Qhat.conj().T)) < 1e-12 * np.abs(Qhat).max()
+    assert np.max(np.abs(Dhat - Dhat.conj().T)) > 1e-3 * np.abs(Dhat).max()   # D_hat itself is not
