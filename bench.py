@@ -565,6 +565,52 @@ def run_op_only(args):
         dist.destroy_process_group()
 
 
+def run_w_mass(args):
+    """One stochastic estimate of W_mass (Sec. 4) on the synthetic field: n factors of the
+    optimal rational approximation on [r_a, r_b] = [0.02, 8], nsrc sources, FP64 CG."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2108_11989_gb300 as qs
+    from synth_inputs import WORKLOADS, kappa_to_m0, make_config, random_spinor
+
+    cfg = make_config(seed=0, **WORKLOADS[args.workload])
+    m = kappa_to_m0(KAPPA)
+    mp = m + 0.002
+    stream = torch.cuda.current_stream()
+    lat = qs.Lattice(cfg.L, cfg.T, stream=stream)
+    lat.load_gauge(cfg.su3, cfg.theta, cfg.csw_su3, cfg.csw_u1)
+    A, nu, mu, delta = qs.ratapprox(args.wm_n, 0.02, 8.0)
+    eta = random_spinor(11, cfg.T, cfg.L, nrhs=args.wm_nsrc).reshape(args.wm_nsrc, -1)
+    dev = torch.from_numpy(np.ascontiguousarray(np.stack([eta.real, eta.imag], -1))).cuda()
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q, lw, iters = lat.w_mass(m, mp, nu, mu, dev, tol=1e-10)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    clk = clocks.stop()
+    ns = cfg.n_sites
+    n_dslash = (4 * iters + 8 * args.wm_n) * args.wm_nsrc     # FP64 operator applications (per RHS)
+    gflops = n_dslash * ns * 2160 / secs / 1e9
+    out = {
+        "metric": "W_mass stochastic estimate (Sec. 4), time per estimate", "value": secs, "unit": "s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "lattice": f"{cfg.L}^3x{cfg.T} (doubled N_s={ns})", "m": m,
+                   "m_prime": mp, "n": args.wm_n, "nsrc": args.wm_nsrc, "r_a": 0.02, "r_b": 8.0,
+                   "ratapprox_delta": delta, "cg_tol": 1e-10},
+        "result": {"log_w_mass": lw, "q": q.tolist(), "cg_iterations": iters},
+        "roofline": {"bound": "alu", "achieved": gflops, "peak": 1250.0, "unit": "GFLOP/s (FP64)",
+                     "frac": gflops / 1250.0, "traffic": None,
+                     "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)",
+                     "flops_model": "2160 flop per site and RHS per FP64 operator application; "
+                                    "4 applications per CG iteration (Q_hat^2), 8 per factor outside"},
+        "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(out))
+    lat.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -588,7 +634,13 @@ def main():
                     help="also time W_sgn in the plain FP64 form (several minutes on 16^3x32)")
     ap.add_argument("--no-big", action="store_true", help="skip the 32^3x64 lines")
     ap.add_argument("--no-big-eig", action="store_true", help="skip the 32^3x64 low-mode solve")
+    ap.add_argument("--w-mass", action="store_true", help="time one W_mass estimate (Sec. 4) instead")
+    ap.add_argument("--wm-n", type=int, default=6, help="order of the rational approximation for --w-mass")
+    ap.add_argument("--wm-nsrc", type=int, default=1, help="sources per factor for --w-mass")
     args = ap.parse_args()
+    if args.w_mass:
+        args.workload = args.workload or WORKLOAD
+        return run_w_mass(args)
     if args.impl == "reference":
         args.workload = args.workload or WORKLOAD
         return run_reference(args)

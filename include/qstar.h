@@ -292,6 +292,34 @@ typedef struct {
                           the negative count; 5 max_steps reached; 6 lambda_bar - r <= 0 */
 } qs_sign_report;
 
+/* Mass reweighting (Sec. 4).
+ *
+ * qs_ratapprox: the order-(n, n) rational function R(y) = A prod_i (y + nu_i^2) / (y + mu_i^2)
+ * with the least uniform relative error |R(y) y^(1/4) - 1| for y in [ra^2, rb^2] (eq.
+ * ratapprox; R(Q_hat^2) replaces (Q_hat^2)^(-1/4) in eq. detQ2, [ra, rb] the range of the
+ * spectrum of |Q_hat|).  Host computation (no GPU work).  0 <= n <= 32, 0 < ra < rb.
+ * nu, mu: HOST arrays of n values, returned in increasing order; *delta the maximal
+ * relative error.  QS_ENOCONV if the Remez iteration does not level the error (orders far
+ * beyond what double precision resolves). */
+QS_API int qs_ratapprox(int n, double ra, double rb, double *A, double *nu, double *mu, double *delta);
+
+/* qs_w_mass: the stochastic estimate of W_mass = det[R(Q_hat_m^2) R^-1(Q_hat_m'^2)] (eq. Wmass)
+ * from the factors j = 1..n, each estimated with the nsrc sources eta as in Sec. 4:
+ *   q[j * nsrc + l] = (eta_l, R_j eta_l),  R_j = X^+ + X + X^+ X,  X = (D_hat(m') - D_hat(m)) S_j,
+ *   *log_w = sum_j log( (1/nsrc) sum_l exp(-q[j * nsrc + l]) ).
+ * The mean of exp(-(eta, R_j eta)) over sources with density ~ exp(-(eta, eta)) estimates
+ * 1/det(1 + R_j), whose product over j is W_mass exactly.  The normalisation A cancels.
+ * nu, mu: HOST arrays of n > 0 values (from qs_ratapprox or any other choice).
+ * eta: DEVICE buffer of nsrc <= 64 FP64 spinors in the canonical layout (complex Gaussian
+ * entries of unit variance; the caller draws them).  Odd-site entries are ignored.
+ * Shifted inverses: FP64 conjugate gradients on Q_hat^2 + shift^2, each to
+ * ||r|| <= tol ||b||, at most max_iter iterations (QS_ENOCONV beyond).  q: HOST array of
+ * n * nsrc; log_w, cg_iterations (total over all solves): HOST, may be NULL.  Allocates
+ * 12 nsrc vectors of work; synchronises the lattice's stream.  QS_EINVAL for odd T or L. */
+QS_API int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const double *nu, const double *mu,
+                     const void *eta, int nsrc, double tol, int max_iter, double *q, double *log_w,
+                     int *cg_iterations);
+
 /* The bounds step A takes from one block of Ritz pairs (host arithmetic, no GPU work):
  * *lambda_bar = min |theta_j| and *lo = min (|theta_j| - res_j) over the values that carry
  * information: the first nwant (the converged ones) and every other one with

@@ -130,6 +130,8 @@ def _load():
         "qs_w_eo": (I, [P, D, D, P, P]),
         "qs_apply_Dhat": (I, [P, D, P, P, I, I]),
         "qs_block_bounds": (I, [P, P, I, I, P, P]),
+        "qs_ratapprox": (I, [I, D, D, P, P, P, P]),
+        "qs_w_mass": (I, [P, D, D, I, P, P, P, I, D, I, P, P, P]),
         "qs_apply_Q_norm2_noalloc": (I, [P, D, P, P, I, I, P]),
         "qs_strerror": (ctypes.c_char_p, [I]),
         "qs_last_cuda_error": (ctypes.c_char_p, []),
@@ -315,6 +317,35 @@ def block_bounds(theta, res, nwant):
     return lb.value, lo.value
 
 
+def ratapprox(n, ra, rb):
+    """qs_ratapprox: (A, nu, mu, delta) of the optimal (n, n) relative approximation of
+    y^-1/4 on [ra^2, rb^2] (host computation)."""
+    A, d = ctypes.c_double(), ctypes.c_double()
+    nu, mu = np.zeros(max(n, 1)), np.zeros(max(n, 1))
+    _check(_lib.qs_ratapprox(int(n), float(ra), float(rb), ctypes.byref(A), nu.ctypes.data, mu.ctypes.data,
+                             ctypes.byref(d)), "ratapprox")
+    return A.value, nu[:n].copy(), mu[:n].copy(), d.value
+
+
+def w_mass(h, m, mp, nu, mu, eta, tol=1e-10, max_iter=20000):
+    """qs_w_mass: (q [n][nsrc], log W_mass estimate, CG iterations); eta a float64 device
+    tensor of nsrc spinors."""
+    import torch
+    if eta.dtype != torch.float64 or not eta.is_cuda or not eta.is_contiguous():
+        raise TypeError("eta must be a contiguous float64 CUDA tensor")
+    nuv = np.ascontiguousarray(nu, dtype=np.float64)
+    muv = np.ascontiguousarray(mu, dtype=np.float64)
+    if nuv.shape != muv.shape or nuv.ndim != 1:
+        raise ValueError("nu and mu must be 1-D arrays of one length")
+    nsrc = _nrhs(h, eta)
+    q = np.zeros(nuv.size * nsrc)
+    lw, it = ctypes.c_double(), ctypes.c_int()
+    _check(_lib.qs_w_mass(h, float(m), float(mp), nuv.size, nuv.ctypes.data, muv.ctypes.data, eta.data_ptr(),
+                          nsrc, float(tol), int(max_iter), q.ctypes.data, ctypes.byref(lw), ctypes.byref(it)),
+           "w_mass")
+    return q.reshape(nuv.size, nsrc), lw.value, it.value
+
+
 def apply_Dhat(h, m0, inp, out, gamma5=False):
     """qs_apply_Dhat: even-odd preconditioned D_hat (or Q_hat) on float64 device spinors."""
     import torch
@@ -496,6 +527,9 @@ class Lattice:
 
     def apply_Dhat(self, m0, inp, out, gamma5=False):
         apply_Dhat(self.h, m0, inp, out, gamma5)
+
+    def w_mass(self, m, mp, nu, mu, eta, tol=1e-10, max_iter=20000):
+        return w_mass(self.h, m, mp, nu, mu, eta, tol, max_iter)
 
     def lowmodes_at_mass(self, m0, opts=None, evecs=None, allow_noconv=False):
         return lowmodes_at_mass(self.h, m0, opts, evecs, allow_noconv)

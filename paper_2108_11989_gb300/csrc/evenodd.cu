@@ -8,6 +8,7 @@
 // sites and counts each twice.  One thread per physical site, a complex LU with
 // partial pivoting per block in FP64, then a fixed-order two-stage sum.
 #include "blas.cuh"
+#include "evenodd.cuh"
 
 #include <math.h>
 #include <stdlib.h>
@@ -270,6 +271,45 @@ __global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const d
 
 }  // namespace
 
+// D_hat (or Q_hat) of nrhs FP64 vectors, asynchronous on the lattice's stream; work holds
+// 3 * nrhs * N_s * 24 doubles.  in and out must not overlap work; in may equal out.
+int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int gamma5, double *work)
+{
+    const Geom &g = lat->g;
+    cudaStream_t st = lat->stream;
+    const int64_t vlen = (int64_t)nrhs * g.Ns * 24;
+    double *x = work, *dx = work + vlen, *w = work + 2 * vlen;
+    double m[64];
+    for (int r = 0; r < nrhs; ++r) m[r] = m0;
+    const int64_t n = g.Ns * 12 * nrhs;
+    const unsigned nb = (unsigned)((n + 255) / 256), nbs = (unsigned)((g.Ns * nrhs + 127) / 128);
+    int s;
+    parity_mask_kernel<<<nb, 256, 0, st>>>((const double2 *)in, (double2 *)x, g, nrhs, 0);
+    qs_note_launches(1);
+    if ((s = qs_dslash_run(lat, QS_F64, m, x, dx, nrhs, 0, 0)) != QS_OK) return s;             // D x
+    clover_solve_odd_kernel<<<nbs, 128, 0, st>>>(lat->clov64, (const double2 *)dx, (double2 *)x, g, nrhs,
+                                                 4.0 + m0);                                      // u (in x)
+    qs_note_launches(1);
+    if ((s = qs_dslash_run(lat, QS_F64, m, x, w, nrhs, 0, 0)) != QS_OK) return s;              // D u
+    even_diff_kernel<<<nb, 256, 0, st>>>((const double2 *)dx, (const double2 *)w, (double2 *)out, g, nrhs,
+                                         gamma5);
+    qs_note_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_dhat_run"); return QS_ECUDA; }
+    return QS_OK;
+}
+
+int qs_even_mask(qs_lattice *lat, const double *in, double *out, int nrhs)
+{
+    const int64_t n = lat->g.Ns * 12 * nrhs;
+    parity_mask_kernel<<<(unsigned)((n + 255) / 256), 256, 0, lat->stream>>>((const double2 *)in, (double2 *)out,
+                                                                             lat->g, nrhs, 0);
+    qs_note_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_even_mask"); return QS_ECUDA; }
+    return QS_OK;
+}
+
 extern "C" int qs_apply_Dhat(qs_lattice *lat, double m0, const void *in, void *out, int nrhs, int gamma5)
 {
     if (!lat || !in || !out || nrhs < 1 || nrhs > 64) return QS_EINVAL;
@@ -281,30 +321,13 @@ extern "C" int qs_apply_Dhat(qs_lattice *lat, double m0, const void *in, void *o
     if (a < b + bytes && b < a + bytes) return QS_EINVAL;
     if (((uintptr_t)in | (uintptr_t)out) & 15) return QS_EINVAL;
     QS_CUDA(cudaSetDevice(lat->device));
-    cudaStream_t st = lat->stream;
     double *buf = nullptr;
     QS_CUDA(cudaMalloc(&buf, 3 * bytes));
-    double *x = buf, *dx = buf + bytes / 8, *w = buf + 2 * bytes / 8;
-    double m[64];
-    for (int r = 0; r < nrhs; ++r) m[r] = m0;
-    const int64_t n = g.Ns * 12 * nrhs;
-    const unsigned nb = (unsigned)((n + 255) / 256), nbs = (unsigned)((g.Ns * nrhs + 127) / 128);
-    int s = QS_OK;
-    do {
-        parity_mask_kernel<<<nb, 256, 0, st>>>((const double2 *)in, (double2 *)x, g, nrhs, 0);
-        qs_note_launches(1);
-        if ((s = qs_dslash_run(lat, QS_F64, m, x, dx, nrhs, 0, 0)) != QS_OK) break;         // D x
-        clover_solve_odd_kernel<<<nbs, 128, 0, st>>>(lat->clov64, (const double2 *)dx, (double2 *)x, g, nrhs,
-                                                     4.0 + m0);                                  // u (in x)
-        qs_note_launches(1);
-        if ((s = qs_dslash_run(lat, QS_F64, m, x, w, nrhs, 0, 0)) != QS_OK) break;          // D u
-        even_diff_kernel<<<nb, 256, 0, st>>>((const double2 *)dx, (const double2 *)w, (double2 *)out, g, nrhs,
-                                             gamma5);
-        qs_note_launches(1);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int s = qs_dhat_run(lat, m0, (const double *)in, (double *)out, nrhs, gamma5, buf);
+    if (s == QS_OK) {
+        const cudaError_t e = cudaStreamSynchronize(lat->stream);
         if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_apply_Dhat"); s = QS_ECUDA; }
-    } while (0);
+    }
     cudaFree(buf);
     return s;
 }

@@ -1,0 +1,12 @@
+// Internal entry points of the even-odd preconditioned operator (Sec. 4), shared by the
+// W_eo / D_hat code and the mass reweighting.
+#pragma once
+#include "qs_internal.cuh"
+
+// D_hat = D_ee - D_eo (D_oo)^-1 D_oe (gamma5 = 1: Q_hat = gamma_5 D_hat) of nrhs FP64 vectors
+// in the canonical layout; odd-site entries of in are ignored, those of out set to zero.
+// Asynchronous on the lattice's stream; work: 3 * nrhs * N_s * 24 doubles; in may equal out.
+int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int gamma5, double *work);
+
+// out = in on the even sites, 0 on the odd ones (nrhs FP64 vectors, asynchronous)
+int qs_even_mask(qs_lattice *lat, const double *in, double *out, int nrhs);
