@@ -270,6 +270,18 @@ typedef struct {
      * step 3 and step B starts from the last certified mass.  1: such a step is first
      * shortened to m + 0.95 lo (the edge of the crossing-free interval around m). */
     int retreat;
+    /* optional path of a JSON-lines log: one line appended per mass visited (step, mass,
+     * phase, lambda_bar, its lower bound, eigensolver work, seconds since the start), or NULL */
+    const char *log_path;
+    /* optional checkpoint file, or NULL.  After every certified mass (the start, each step-A
+     * step, each counted step-B step) the flow state -- target mass, the certified mass, the
+     * crossings counted up to it, steps taken, the lattice's extents, C* mask and c_sw's --
+     * is written as one JSON object, atomically (temporary file, then rename). */
+    const char *checkpoint_path;
+    /* 1: if checkpoint_path exists and was written for the same target mass and lattice,
+     * continue the flow from its certified mass with its crossing count (the window there
+     * is solved again); otherwise start from the target.  0: always start from the target. */
+    int resume;
 } qs_sign_opts;
 
 typedef struct {
@@ -290,6 +302,8 @@ typedef struct {
                           spectral gap; 3 a step-B count was not certified (bounds straddle
                           the gap, or the window does not reach above it); 4 odd change of
                           the negative count; 5 max_steps reached; 6 lambda_bar - r <= 0 */
+    int checkpoint_errors;   /* checkpoints that could not be written (the flow goes on) */
+    double resumed_from;     /* the certified mass a resumed flow started from (else m0_target) */
 } qs_sign_report;
 
 /* Mass reweighting (Sec. 4).

@@ -61,7 +61,8 @@ QS_WINDOW = 24
 class SignOpts(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("m0_max", ctypes.c_double), ("max_steps", ctypes.c_int),
                 ("eig", EigOpts), ("step_model", ctypes.c_void_p),
-                ("window_trace", ctypes.POINTER(ctypes.c_double)), ("retreat", ctypes.c_int)]
+                ("window_trace", ctypes.POINTER(ctypes.c_double)), ("retreat", ctypes.c_int),
+                ("log_path", ctypes.c_char_p), ("checkpoint_path", ctypes.c_char_p), ("resume", ctypes.c_int)]
 
 
 class SignReport(ctypes.Structure):
@@ -72,7 +73,8 @@ class SignReport(ctypes.Structure):
                 ("dslash_f32", ctypes.c_int64), ("dslash_f64", ctypes.c_int64),
                 ("cg_iterations", ctypes.c_int64), ("seconds", ctypes.c_double),
                 ("learned_accepted", ctypes.c_int), ("learned_rejected", ctypes.c_int),
-                ("fail_reason", ctypes.c_int)]
+                ("fail_reason", ctypes.c_int), ("checkpoint_errors", ctypes.c_int),
+                ("resumed_from", ctypes.c_double)]
 
     def as_dict(self):
         n = min(self.n, QS_TRACE_MAX)
@@ -82,7 +84,8 @@ class SignReport(ctypes.Structure):
                 "dslash_f32": self.dslash_f32, "dslash_f64": self.dslash_f64,
                 "cg_iterations": self.cg_iterations, "seconds": self.seconds,
                 "learned_accepted": self.learned_accepted, "learned_rejected": self.learned_rejected,
-                "fail_reason": self.fail_reason}
+                "fail_reason": self.fail_reason, "checkpoint_errors": self.checkpoint_errors,
+                "resumed_from": self.resumed_from}
 
 
 class KernelProf(ctypes.Structure):
@@ -245,6 +248,8 @@ def sign_default_opts(eig=None, **kw):
     o = SignOpts()
     _lib.qs_sign_default_opts(ctypes.byref(o))
     for k, v in kw.items():
+        if k in ("log_path", "checkpoint_path") and isinstance(v, (str, os.PathLike)):
+            v = os.fsencode(v)
         setattr(o, k, v)
     if eig is not None:
         for k, v in (eig.items() if isinstance(eig, dict) else []):

@@ -25,7 +25,10 @@
 // the sign.  Back to step A as soon as lambda_bar grows again.
 #include "blas.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 #include <time.h>
 
@@ -43,6 +46,9 @@ extern "C" void qs_sign_default_opts(qs_sign_opts *o)
     o->step_model = nullptr;
     o->window_trace = nullptr;
     o->retreat = 0;
+    o->log_path = nullptr;
+    o->checkpoint_path = nullptr;
+    o->resume = 0;
     qs_eig_default_opts(&o->eig);
     // certificates carry the residual bound r, so any r < |theta| is rigorous; a
     // moderate relative accuracy keeps every mass point cheap
@@ -110,19 +116,35 @@ int modes(Flow &f, double m, char phase, Ritz *rz)
     int conv = 0;
     qs_eig_stats st;
     memset(&st, 0, sizeof(st));
+    char label[64];
+    snprintf(label, sizeof(label), "modes %c m=%.6f", phase, m);
+    nvtxRangePushA(label);
     int s = qs_lowmodes_impl(f.lat, m, &e, rz, &conv, &st);
+    nvtxRangePop();
     if (s != QS_OK) { f.rep->fail_reason = 1; return s; }
     qs_sign_report *r = f.rep;
     r->dslash_f32 += st.dslash_f32;
     r->dslash_f64 += st.dslash_f64;
     r->cg_iterations += st.cg_iterations;
+    double lb, lo;
+    lambda_bar(*rz, e.k, e.nwant, &lb, &lo);
     if (r->n < QS_TRACE_MAX) {
         r->mass[r->n] = m;
-        double lb, lo;
-        lambda_bar(*rz, e.k, e.nwant, &lb, &lo);
         r->lambda_bar[r->n] = lb;
         r->resid[r->n] = lb - lo;
         r->phase[r->n] = phase;
+    }
+    if (f.o.log_path) {   // one JSON line per mass visited, appended
+        FILE *fp = fopen(f.o.log_path, "a");
+        if (fp) {
+            fprintf(fp,
+                    "{\"step\": %d, \"mass\": %.17g, \"phase\": \"%c\", \"lambda_bar\": %.17g, "
+                    "\"lower_bound\": %.17g, \"converged\": %d, \"dslash_f32\": %lld, \"dslash_f64\": %lld, "
+                    "\"cg_iterations\": %lld, \"seconds\": %.6f}\n",
+                    r->n, m, phase, lb, lo, conv, (long long)st.dslash_f32, (long long)st.dslash_f64,
+                    (long long)st.cg_iterations, now_s() - f.t0);
+            fclose(fp);
+        }
     }
     if (f.o.window_trace && r->n < f.o.max_steps)
         for (int i = 0; i < QS_WINDOW; ++i)
@@ -164,6 +186,95 @@ int propose(Flow &f, double lb, double *dm)
     return QS_OK;
 }
 
+// ---- checkpoint of the flow at a certified mass -----------------------------------------
+struct Checkpoint {
+    double m_target, m, csw_su3, csw_u1;
+    long flips;
+    int crossings, steps, L, T, cstar_y, cstar_z, t_anti;
+};
+
+bool write_checkpoint(const char *path, const Checkpoint &c)
+{
+    char tmp[4096];
+    if (snprintf(tmp, sizeof(tmp), "%s.tmp", path) >= (int)sizeof(tmp)) return false;
+    FILE *fp = fopen(tmp, "w");
+    if (!fp) return false;
+    const int n = fprintf(fp,
+                          "{\"qstar_sign_checkpoint\": 1, \"m_target\": %.17g, \"m\": %.17g, \"flips\": %ld, "
+                          "\"crossings\": %d, \"steps\": %d, \"L\": %d, \"T\": %d, \"cstar_y\": %d, "
+                          "\"cstar_z\": %d, \"t_anti\": %d, \"csw_su3\": %.17g, \"csw_u1\": %.17g}\n",
+                          c.m_target, c.m, c.flips, c.crossings, c.steps, c.L, c.T, c.cstar_y, c.cstar_z, c.t_anti,
+                          c.csw_su3, c.csw_u1);
+    const bool ok = n > 0 && fflush(fp) == 0;
+    if (fclose(fp) != 0 || !ok) { remove(tmp); return false; }
+    return rename(tmp, path) == 0;
+}
+
+// the number after "key": in a one-object JSON text; false if the key is missing
+bool json_number(const char *txt, const char *key, double *v)
+{
+    char pat[64];
+    snprintf(pat, sizeof(pat), "\"%s\":", key);
+    const char *p = strstr(txt, pat);
+    if (!p) return false;
+    char *end = nullptr;
+    *v = strtod(p + strlen(pat), &end);
+    return end != p + strlen(pat);
+}
+
+bool read_checkpoint(const char *path, Checkpoint *c)
+{
+    FILE *fp = fopen(path, "r");
+    if (!fp) return false;
+    char txt[2048];
+    const size_t n = fread(txt, 1, sizeof(txt) - 1, fp);
+    fclose(fp);
+    txt[n] = 0;
+    double v[13];
+    const char *keys[13] = {"qstar_sign_checkpoint", "m_target", "m", "flips", "crossings", "steps", "L", "T",
+                            "cstar_y", "cstar_z", "t_anti", "csw_su3", "csw_u1"};
+    for (int i = 0; i < 13; ++i)
+        if (!json_number(txt, keys[i], &v[i])) return false;
+    if (v[0] != 1) return false;
+    c->m_target = v[1];
+    c->m = v[2];
+    c->flips = (long)v[3];
+    c->crossings = (int)v[4];
+    c->steps = (int)v[5];
+    c->L = (int)v[6];
+    c->T = (int)v[7];
+    c->cstar_y = (int)v[8];
+    c->cstar_z = (int)v[9];
+    c->t_anti = (int)v[10];
+    c->csw_su3 = v[11];
+    c->csw_u1 = v[12];
+    return true;
+}
+
+Checkpoint state_of(const Flow &f, double m_target, double m, long flips)
+{
+    Checkpoint c;
+    c.m_target = m_target;
+    c.m = m;
+    c.flips = flips;
+    c.crossings = f.rep->crossings;
+    c.steps = f.steps;
+    c.L = f.lat->g.L;
+    c.T = f.lat->g.T;
+    c.cstar_y = f.lat->g.cstar_y;
+    c.cstar_z = f.lat->g.cstar_z;
+    c.t_anti = f.lat->g.t_anti;
+    c.csw_su3 = f.lat->csw_su3;
+    c.csw_u1 = f.lat->csw_u1;
+    return c;
+}
+
+bool same_problem(const Checkpoint &a, const Checkpoint &b)
+{
+    return a.m_target == b.m_target && a.L == b.L && a.T == b.T && a.cstar_y == b.cstar_y &&
+           a.cstar_z == b.cstar_z && a.t_anti == b.t_anti && a.csw_su3 == b.csw_su3 && a.csw_u1 == b.csw_u1;
+}
+
 }  // namespace
 
 extern "C" int qs_block_bounds(const double *theta, const double *res, int k, int nwant, double *lb, double *lo)
@@ -200,9 +311,11 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
         }
     }
     f.t0 = now_s();
+    nvtxRangePushA("qs_pfaffian_sign");
     const double m0max = f.o.m0_max > 0 ? f.o.m0_max : 3.0 * (lat->csw_su3 + lat->csw_u1);
     int st;
     auto finish = [&](int status) {
+        nvtxRangePop();
         rep->seconds = now_s() - f.t0;
         cudaFree(f.dX);
         cudaFree(f.dY);
@@ -210,6 +323,23 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
     };
 
     double m = m_target;
+    long flips = 0;
+    rep->resumed_from = m_target;
+    if (f.o.resume && f.o.checkpoint_path) {
+        // continue from the certified mass of an earlier run on the same problem
+        Checkpoint c;
+        if (read_checkpoint(f.o.checkpoint_path, &c) && same_problem(c, state_of(f, m_target, m, 0))) {
+            m = c.m;
+            rep->resumed_from = m;
+            flips = c.flips;
+            rep->crossings = c.crossings;
+            f.steps = c.steps;
+        }
+    }
+    auto checkpoint = [&]() {
+        if (f.o.checkpoint_path && !write_checkpoint(f.o.checkpoint_path, state_of(f, m_target, m, flips)))
+            rep->checkpoint_errors++;
+    };
     const int kk = f.o.eig.k, nw = f.o.eig.nwant;
     Ritz cur;
     st = modes(f, m, 'A', &cur);
@@ -219,7 +349,7 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
         lambda_bar(cur, kk, nw, &lb0, &lo0);
         if (!(lo0 > 0)) { rep->fail_reason = 6; return finish(QS_EUNDECIDED); }
     }
-    long flips = 0;
+    checkpoint();
     while (f.steps < f.o.max_steps) {
         // ---- step A -------------------------------------------------------------
         bool go_b = false;
@@ -275,6 +405,7 @@ extern "C" int qs_pfaffian_sign(qs_lattice *lat, double m_target, const qs_sign_
             }
             m = mn;
             cur = nw_r;
+            if (lo2 > 0) checkpoint();   // a certified mass from which step A can restart
             if (lb2 < lb) { go_b = true; break; }   // step 3: lambda_bar decreases
         }
         if (!go_b) break;

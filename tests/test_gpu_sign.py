@@ -120,3 +120,34 @@ def test_block_bounds_certify_the_exact_spectrum(qs):
         assert lo <= exact + 1e-12 and exact <= lb + 1e-6, (m, lo, exact, lb)
         assert exact - lo < 1e-6 * max(1.0, exact)
     lat.close()
+
+
+def test_checkpoint_resume_and_step_log(qs, tmp_path):
+    """The JSON-lines log has one line per mass visited; a flow cut short by max_steps and
+    resumed from its last certified mass gives the uninterrupted flow's (and the oracle's)
+    sign; a checkpoint of another target mass is ignored."""
+    cfg = make_config(T=4, L=2, eps=2.0, theta_sigma=0.3, csw_su3=1.5, csw_u1=1.0, seed=2)
+    op = WilsonDirac(cfg)
+    lat = lattice(qs, cfg)
+    eig = {"k": 16, "nwant": 2, "tol": 1e-6, "cheb_degree": 16}
+    m = -1.65
+    log, ck, ck2 = tmp_path / "flow.jsonl", tmp_path / "full.json", tmp_path / "cut.json"
+    s_full, rep = lat.pfaffian_sign(m, qs.sign_default_opts(eig=eig, log_path=log, checkpoint_path=ck))
+    assert s_full == sign_by_eigencount(op, m)
+    lines = [json.loads(x) for x in open(log)]
+    assert [x["mass"] for x in lines] == rep["mass"] and "".join(x["phase"] for x in lines) == rep["phase"]
+    assert all(x["lower_bound"] <= x["lambda_bar"] for x in lines)
+    saved = json.load(open(ck))
+    assert saved["m_target"] == m and saved["m"] in rep["mass"] and rep["checkpoint_errors"] == 0
+    assert rep["n"] > 3
+    with pytest.raises(qs.QStarError):
+        lat.pfaffian_sign(m, qs.sign_default_opts(eig=eig, max_steps=3, checkpoint_path=ck2))
+    cut = json.load(open(ck2))
+    assert cut["m"] > m and cut["steps"] <= 3
+    s_res, rep_res = lat.pfaffian_sign(m, qs.sign_default_opts(eig=eig, checkpoint_path=ck2, resume=1))
+    assert s_res == s_full and rep_res["resumed_from"] == cut["m"]
+    assert rep_res["mass"][0] == cut["m"]
+    # another target: the checkpoint does not apply and the flow starts from the target
+    s_other, rep_other = lat.pfaffian_sign(-1.5, qs.sign_default_opts(eig=eig, checkpoint_path=ck2, resume=1))
+    assert rep_other["resumed_from"] == -1.5 and s_other == sign_by_eigencount(op, -1.5)
+    lat.close()
