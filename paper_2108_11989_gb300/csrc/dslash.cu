@@ -343,6 +343,25 @@ __global__ void __launch_bounds__(128) dslash_batch_kernel(BatchArgs<R> a)
     dslash_site<R, SOA>(it.g, it.links, it.clov, it.in, it.out, a.gamma5, it.m0[r], r, s);
 }
 
+// The FP64 operator on the sites of one parity only ((t + z + y + x) mod 2 == parity);
+// sites of the other parity get zeros.  The even-odd preconditioned operator needs one
+// parity of the output of each of its two applications.
+__global__ void __launch_bounds__(128) dslash64_parity_kernel(DslashArgs<double> a, int parity)
+{
+    const unsigned b = blockIdx.x;
+    const int r = (int)(b % (unsigned)a.nrhs);
+    const int s = (int)(b / (unsigned)a.nrhs) * 128 + (int)threadIdx.x;
+    if (s >= (int)a.g.Ns) return;
+    const Site c = site_of(a.g, s);
+    if (((c.t + c.z + c.y + c.x) & 1) != parity) {
+        double2 *o = (double2 *)(a.out + ((int64_t)r * a.g.Ns + s) * 24);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) o[i] = make_double2(0.0, 0.0);
+        return;
+    }
+    dslash_site<double, false>(a.g, a.links, a.clov, a.in, a.out, a.gamma5, a.m0[r], r, s);
+}
+
 }  // namespace
 
 template <typename R, int MINB>
@@ -370,6 +389,13 @@ cudaError_t qs_dslash_launch<double>(DslashArgs<double> a, int nrhs, int variant
     case 2: return launch_variant<double, 3>(a, soa, st);
     default: return launch_variant<double, 4>(a, soa, st);
     }
+}
+
+cudaError_t qs_dslash64_parity_launch(const DslashArgs<double> &a, int parity, cudaStream_t st)
+{
+    const int64_t nb = ((a.g.Ns + 127) / 128) * a.nrhs;
+    dslash64_parity_kernel<<<(unsigned)nb, 128, 0, st>>>(a, parity);
+    return cudaGetLastError();
 }
 
 // canonical [site][12][re, im] <-> solver [site / 16][12][site % 16][re, im], per vector

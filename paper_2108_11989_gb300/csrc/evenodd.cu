@@ -170,27 +170,13 @@ __global__ void parity_mask_kernel(const double2 *__restrict__ in, double2 *__re
     out[i] = site_parity(g, s) == keep ? in[i] : make_double2(0, 0);
 }
 
-// out_e = a_e - b_e (gamma_5 applied if asked), 0 on odd sites
-__global__ void even_diff_kernel(const double2 *__restrict__ a, const double2 *__restrict__ b,
-                                 double2 *__restrict__ out, Geom g, int k, int gamma5)
-{
-    const int64_t n = g.Ns * 12 * k;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t s = (i / 12) % g.Ns;
-    const int comp = (int)(i % 12);
-    if (site_parity(g, s) != 0) { out[i] = make_double2(0, 0); return; }
-    double2 v = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
-    if (gamma5 && comp >= 6) v = make_double2(-v.x, -v.y);
-    out[i] = v;
-}
-
-// u = (4 + m0 + A(x))^-1 t on odd sites (two 6 x 6 chiral blocks, complex Gaussian
-// elimination with partial pivoting in FP64), 0 on even sites; one thread per (vector, site).
+// v = x on even sites and v = -(4 + m0 + A(x))^-1 t on odd sites (two 6 x 6 chiral blocks,
+// complex Gaussian elimination with partial pivoting in FP64); one thread per (vector, site).
 // The mirror site's block is S conj(A) S: entry (i, j) = sign * conj(A[i +- 3][j +- 3]),
 // sign = -1 across the two spin halves.
 __global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const double2 *__restrict__ t,
-                                        double2 *__restrict__ u, Geom g, int k, double dm)
+                                        const double2 *__restrict__ xe, double2 *__restrict__ u, Geom g, int k,
+                                        double dm)
 {
     const int64_t n = g.Ns * k;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -199,7 +185,8 @@ __global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const d
     const double2 *ti = t + i * 12;
     double2 *ui = u + i * 12;
     if (site_parity(g, s) == 0) {
-        for (int c = 0; c < 12; ++c) ui[c] = make_double2(0, 0);
+        const double2 *xi = xe + i * 12;
+        for (int c = 0; c < 12; ++c) ui[c] = xi[c];
         return;
     }
     const int x = (int)(s % g.L2);
@@ -265,7 +252,7 @@ __global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const d
             rr[r] = (sr * ar[r][r] + si * ai[r][r]) / d2;
             ri[r] = (si * ar[r][r] - sr * ai[r][r]) / d2;
         }
-        for (int r = 0; r < 6; ++r) ui[6 * b + r] = make_double2(rr[r], ri[r]);
+        for (int r = 0; r < 6; ++r) ui[6 * b + r] = make_double2(-rr[r], -ri[r]);
     }
 }
 
@@ -273,28 +260,38 @@ __global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const d
 
 // D_hat (or Q_hat) of nrhs FP64 vectors, asynchronous on the lattice's stream; work holds
 // 3 * nrhs * N_s * 24 doubles.  in and out must not overlap work; in may equal out.
+// With x the even part of the input, u = (D_oo)^-1 (D x)_o and v = x - u (even part x,
+// odd part -u):  D_hat x = (D x)_e - (D u)_e = (D v)_e, so the operator is applied twice,
+// each time on the output sites of one parity only.
 int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int gamma5, double *work)
 {
     const Geom &g = lat->g;
     cudaStream_t st = lat->stream;
     const int64_t vlen = (int64_t)nrhs * g.Ns * 24;
-    double *x = work, *dx = work + vlen, *w = work + 2 * vlen;
-    double m[64];
-    for (int r = 0; r < nrhs; ++r) m[r] = m0;
+    double *x = work, *dx = work + vlen, *v = work + 2 * vlen;
+    DslashArgs<double> d;
+    d.g = g;
+    d.links = lat->links64;
+    d.clov = lat->clov64;
+    d.nrhs = nrhs;
+    for (int r = 0; r < nrhs; ++r) d.m0[r] = m0;
     const int64_t n = g.Ns * 12 * nrhs;
     const unsigned nb = (unsigned)((n + 255) / 256), nbs = (unsigned)((g.Ns * nrhs + 127) / 128);
-    int s;
     parity_mask_kernel<<<nb, 256, 0, st>>>((const double2 *)in, (double2 *)x, g, nrhs, 0);
-    qs_note_launches(1);
-    if ((s = qs_dslash_run(lat, QS_F64, m, x, dx, nrhs, 0, 0)) != QS_OK) return s;             // D x
-    clover_solve_odd_kernel<<<nbs, 128, 0, st>>>(lat->clov64, (const double2 *)dx, (double2 *)x, g, nrhs,
-                                                 4.0 + m0);                                      // u (in x)
-    qs_note_launches(1);
-    if ((s = qs_dslash_run(lat, QS_F64, m, x, w, nrhs, 0, 0)) != QS_OK) return s;              // D u
-    even_diff_kernel<<<nb, 256, 0, st>>>((const double2 *)dx, (const double2 *)w, (double2 *)out, g, nrhs,
-                                         gamma5);
-    qs_note_launches(1);
-    const cudaError_t e = cudaGetLastError();
+    d.in = x;
+    d.out = dx;
+    d.gamma5 = 0;
+    cudaError_t e = qs_dslash64_parity_launch(d, 1, st);                                     // (D x)_o
+    if (e == cudaSuccess) {
+        clover_solve_odd_kernel<<<nbs, 128, 0, st>>>(lat->clov64, (const double2 *)dx, (const double2 *)x,
+                                                     (double2 *)v, g, nrhs, 4.0 + m0);       // v = x - u
+        d.in = v;
+        d.out = out;
+        d.gamma5 = gamma5;
+        e = qs_dslash64_parity_launch(d, 0, st);                                             // (D v)_e
+    }
+    qs_note_launches(4);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_dhat_run"); return QS_ECUDA; }
     return QS_OK;
 }

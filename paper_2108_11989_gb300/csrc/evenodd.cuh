@@ -1,7 +1,12 @@
 // Internal entry points of the even-odd preconditioned operator (Sec. 4), shared by the
 // W_eo / D_hat code and the mass reweighting.
 #pragma once
+#include "dslash.cuh"
 #include "qs_internal.cuh"
+
+// the FP64 operator on the output sites of one parity ((t + z + y + x) mod 2), zeros on the
+// others; canonical layout (dslash.cu)
+cudaError_t qs_dslash64_parity_launch(const DslashArgs<double> &a, int parity, cudaStream_t st);
 
 // D_hat = D_ee - D_eo (D_oo)^-1 D_oe (gamma5 = 1: Q_hat = gamma_5 D_hat) of nrhs FP64 vectors
 // in the canonical layout; odd-site entries of in are ignored, those of out set to zero.

@@ -139,15 +139,19 @@ def test_checkpoint_resume_and_step_log(qs, tmp_path):
     assert all(x["lower_bound"] <= x["lambda_bar"] for x in lines)
     saved = json.load(open(ck))
     assert saved["m_target"] == m and saved["m"] in rep["mass"] and rep["checkpoint_errors"] == 0
-    assert rep["n"] > 3
+    # cut short and resumed: at m = 0.3, away from the crossings, step A certifies its steps,
+    # so the cut flow leaves a checkpoint beyond the target
+    m2 = 0.3
+    s_a, rep_a = lat.pfaffian_sign(m2, qs.sign_default_opts(eig=eig))
+    assert rep_a["n"] > 3 and s_a == sign_by_eigencount(op, m2)
     with pytest.raises(qs.QStarError):
-        lat.pfaffian_sign(m, qs.sign_default_opts(eig=eig, max_steps=3, checkpoint_path=ck2))
+        lat.pfaffian_sign(m2, qs.sign_default_opts(eig=eig, max_steps=2, checkpoint_path=ck2))
     cut = json.load(open(ck2))
-    assert cut["m"] > m and cut["steps"] <= 3
-    s_res, rep_res = lat.pfaffian_sign(m, qs.sign_default_opts(eig=eig, checkpoint_path=ck2, resume=1))
-    assert s_res == s_full and rep_res["resumed_from"] == cut["m"]
+    assert cut["m"] > m2 and cut["steps"] <= 2 and cut["m"] in rep_a["mass"]
+    s_res, rep_res = lat.pfaffian_sign(m2, qs.sign_default_opts(eig=eig, checkpoint_path=ck2, resume=1))
+    assert s_res == s_a and rep_res["resumed_from"] == cut["m"]
     assert rep_res["mass"][0] == cut["m"]
     # another target: the checkpoint does not apply and the flow starts from the target
-    s_other, rep_other = lat.pfaffian_sign(-1.5, qs.sign_default_opts(eig=eig, checkpoint_path=ck2, resume=1))
-    assert rep_other["resumed_from"] == -1.5 and s_other == sign_by_eigencount(op, -1.5)
+    s_other, rep_other = lat.pfaffian_sign(m, qs.sign_default_opts(eig=eig, checkpoint_path=ck2, resume=1))
+    assert rep_other["resumed_from"] == m and s_other == s_full
     lat.close()
