@@ -591,7 +591,9 @@ def run_w_mass(args):
     secs = time.perf_counter() - t0
     clk = clocks.stop()
     ns = cfg.n_sites
-    n_dslash = (4 * iters + 8 * args.wm_n) * args.wm_nsrc     # FP64 operator applications (per RHS)
+    # full-lattice equivalents of the FP64 operator (per RHS): D_hat applies it to each parity
+    # once, Q_hat^2 twice per CG iteration, four more D_hat per factor outside the CG
+    n_dslash = (2 * iters + 4 * args.wm_n) * args.wm_nsrc
     gflops = n_dslash * ns * 2160 / secs / 1e9
     out = {
         "metric": "W_mass stochastic estimate (Sec. 4), time per estimate", "value": secs, "unit": "s",
@@ -603,8 +605,10 @@ def run_w_mass(args):
         "roofline": {"bound": "alu", "achieved": gflops, "peak": 1250.0, "unit": "GFLOP/s (FP64)",
                      "frac": gflops / 1250.0, "traffic": None,
                      "peak_source": "nominal FP64 rate of GB300 (no measured FP64 peak)",
-                     "flops_model": "2160 flop per site and RHS per FP64 operator application; "
-                                    "4 applications per CG iteration (Q_hat^2), 8 per factor outside"},
+                     "flops_model": "2160 flop per site and RHS per full-lattice FP64 operator "
+                                    "application; D_hat = one (half on each parity); Q_hat^2 per CG "
+                                    "iteration = two; four D_hat per factor outside the CG; the odd-site "
+                                    "block solves are not counted"},
         "gpu_launches": None, "clocks": clk,
     }
     print(json.dumps(out))

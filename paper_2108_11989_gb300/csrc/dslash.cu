@@ -345,20 +345,23 @@ __global__ void __launch_bounds__(128) dslash_batch_kernel(BatchArgs<R> a)
 
 // The FP64 operator on the sites of one parity only ((t + z + y + x) mod 2 == parity);
 // sites of the other parity get zeros.  The even-odd preconditioned operator needs one
-// parity of the output of each of its two applications.
+// parity of the output of each of its two applications.  Thread j handles the j-th site of
+// that parity (a row of 2L sites holds L of each, at x = 2 jx or 2 jx + 1), so the warps
+// hold sites of one parity only, and it writes zeros to the other site of its x pair.
 __global__ void __launch_bounds__(128) dslash64_parity_kernel(DslashArgs<double> a, int parity)
 {
     const unsigned b = blockIdx.x;
     const int r = (int)(b % (unsigned)a.nrhs);
-    const int s = (int)(b / (unsigned)a.nrhs) * 128 + (int)threadIdx.x;
-    if (s >= (int)a.g.Ns) return;
-    const Site c = site_of(a.g, s);
-    if (((c.t + c.z + c.y + c.x) & 1) != parity) {
-        double2 *o = (double2 *)(a.out + ((int64_t)r * a.g.Ns + s) * 24);
+    const int j = (int)(b / (unsigned)a.nrhs) * 128 + (int)threadIdx.x;
+    if (j >= (int)(a.g.Ns / 2)) return;
+    const int row = j / a.g.L;
+    const int jx = j - row * a.g.L;
+    const int y = row % a.g.L, z = (row / a.g.L) % a.g.L, t = row / (a.g.L * a.g.L);
+    const int x = 2 * jx + ((parity + t + z + y) & 1);
+    const int s = row * a.g.L2 + x;
+    double2 *o = (double2 *)(a.out + ((int64_t)r * a.g.Ns + (s ^ 1)) * 24);
 #pragma unroll
-        for (int i = 0; i < 12; ++i) o[i] = make_double2(0.0, 0.0);
-        return;
-    }
+    for (int i = 0; i < 12; ++i) o[i] = make_double2(0.0, 0.0);
     dslash_site<double, false>(a.g, a.links, a.clov, a.in, a.out, a.gamma5, a.m0[r], r, s);
 }
 
@@ -393,7 +396,7 @@ cudaError_t qs_dslash_launch<double>(DslashArgs<double> a, int nrhs, int variant
 
 cudaError_t qs_dslash64_parity_launch(const DslashArgs<double> &a, int parity, cudaStream_t st)
 {
-    const int64_t nb = ((a.g.Ns + 127) / 128) * a.nrhs;
+    const int64_t nb = ((a.g.Ns / 2 + 127) / 128) * a.nrhs;
     dslash64_parity_kernel<<<(unsigned)nb, 128, 0, st>>>(a, parity);
     return cudaGetLastError();
 }

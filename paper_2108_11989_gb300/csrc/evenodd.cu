@@ -256,6 +256,113 @@ __global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const d
     }
 }
 
+// inv = (4 + m0 + A(x))^-1 for every odd physical site x, both chiral blocks, by Gauss-Jordan
+// elimination with partial pivoting in FP64; layout [block][6][6][V_phys] complex (entries of
+// even sites are left untouched).  The mirror site's block S conj(M) S has the inverse
+// S conj(M^-1) S, formed on the fly when it is applied.
+__global__ void clover_inverse_kernel(const double *__restrict__ clov, Geom g, double dm, double2 *__restrict__ inv)
+{
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= g.Vphys) return;
+    const int x = (int)(p % g.L);
+    int64_t row = p / g.L;
+    const int y = (int)(row % g.L);
+    row /= g.L;
+    const int z = (int)(row % g.L);
+    const int t = (int)(row / g.L);
+    if (((t + z + y + x) & 1) == 0) return;
+    const int64_t V = g.Vphys;
+    for (int b = 0; b < 2; ++b) {
+        const double *cb = clov + (int64_t)b * 36 * V + p;
+        double ar[6][6], ai[6][6], br[6][6], bi[6][6];
+        for (int i = 0; i < 6; ++i) {
+            ar[i][i] = dm + cb[(int64_t)i * V];
+            ai[i][i] = 0.0;
+            for (int j = 0; j < i; ++j) {
+                const int k = 6 + 2 * qs_tri(i, j);
+                ar[i][j] = cb[(int64_t)k * V];
+                ai[i][j] = cb[(int64_t)(k + 1) * V];
+                ar[j][i] = ar[i][j];      // Hermitian: upper = conj(lower)
+                ai[j][i] = -ai[i][j];
+            }
+            for (int j = 0; j < 6; ++j) { br[i][j] = i == j ? 1.0 : 0.0; bi[i][j] = 0.0; }
+        }
+        for (int c = 0; c < 6; ++c) {
+            int piv = c;
+            double best = ar[c][c] * ar[c][c] + ai[c][c] * ai[c][c];
+            for (int r = c + 1; r < 6; ++r) {
+                const double a2 = ar[r][c] * ar[r][c] + ai[r][c] * ai[r][c];
+                if (a2 > best) { best = a2; piv = r; }
+            }
+            if (piv != c)
+                for (int j = 0; j < 6; ++j) {
+                    double q = ar[c][j]; ar[c][j] = ar[piv][j]; ar[piv][j] = q;
+                    q = ai[c][j]; ai[c][j] = ai[piv][j]; ai[piv][j] = q;
+                    q = br[c][j]; br[c][j] = br[piv][j]; br[piv][j] = q;
+                    q = bi[c][j]; bi[c][j] = bi[piv][j]; bi[piv][j] = q;
+                }
+            const double pr = ar[c][c] / best, pim = -ai[c][c] / best;   // 1 / pivot
+            for (int j = 0; j < 6; ++j) {
+                double q = ar[c][j] * pr - ai[c][j] * pim;
+                ai[c][j] = ar[c][j] * pim + ai[c][j] * pr;
+                ar[c][j] = q;
+                q = br[c][j] * pr - bi[c][j] * pim;
+                bi[c][j] = br[c][j] * pim + bi[c][j] * pr;
+                br[c][j] = q;
+            }
+            for (int r = 0; r < 6; ++r) {
+                if (r == c) continue;
+                const double fr = ar[r][c], fi = ai[r][c];
+                for (int j = 0; j < 6; ++j) {
+                    ar[r][j] -= fr * ar[c][j] - fi * ai[c][j];
+                    ai[r][j] -= fr * ai[c][j] + fi * ar[c][j];
+                    br[r][j] -= fr * br[c][j] - fi * bi[c][j];
+                    bi[r][j] -= fr * bi[c][j] + fi * br[c][j];
+                }
+            }
+        }
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) inv[((int64_t)b * 36 + i * 6 + j) * V + p] = make_double2(br[i][j], bi[i][j]);
+    }
+}
+
+// v = x on even sites, v = -(4 + m0 + A(x))^-1 t on odd sites from the stored inverses
+__global__ void clover_apply_inv_kernel(const double2 *__restrict__ inv, const double2 *__restrict__ t,
+                                        const double2 *__restrict__ xe, double2 *__restrict__ v, Geom g, int k)
+{
+    const int64_t n = g.Ns * k;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t s = i % g.Ns;
+    double2 *vi = v + i * 12;
+    if (site_parity(g, s) == 0) {
+        const double2 *xi = xe + i * 12;
+        for (int c = 0; c < 12; ++c) vi[c] = xi[c];
+        return;
+    }
+    const double2 *ti = t + i * 12;
+    const int x = (int)(s % g.L2);
+    const bool mir = x >= g.L;
+    const int64_t p = (s / g.L2) * g.L + (mir ? x - g.L : x);
+    const int64_t V = g.Vphys;
+    for (int b = 0; b < 2; ++b)
+        for (int r = 0; r < 6; ++r) {
+            double accr = 0, acci = 0;
+            for (int c = 0; c < 6; ++c) {
+                const int ii = mir ? (r + 3) % 6 : r, jj = mir ? (c + 3) % 6 : c;
+                double2 e = inv[((int64_t)b * 36 + ii * 6 + jj) * V + p];
+                if (mir) {
+                    e.y = -e.y;
+                    if ((r < 3) != (c < 3)) { e.x = -e.x; e.y = -e.y; }
+                }
+                const double2 q = ti[6 * b + c];
+                accr += e.x * q.x - e.y * q.y;
+                acci += e.x * q.y + e.y * q.x;
+            }
+            vi[6 * b + r] = make_double2(-accr, -acci);
+        }
+}
+
 }  // namespace
 
 // D_hat (or Q_hat) of nrhs FP64 vectors, asynchronous on the lattice's stream; work holds
@@ -263,7 +370,18 @@ __global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const d
 // With x the even part of the input, u = (D_oo)^-1 (D x)_o and v = x - u (even part x,
 // odd part -u):  D_hat x = (D x)_e - (D u)_e = (D v)_e, so the operator is applied twice,
 // each time on the output sites of one parity only.
-int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int gamma5, double *work)
+int qs_clover_inverse_odd(qs_lattice *lat, double m0, double2 *inv)
+{
+    const int64_t V = lat->g.Vphys;
+    clover_inverse_kernel<<<(unsigned)((V + 127) / 128), 128, 0, lat->stream>>>(lat->clov64, lat->g, 4.0 + m0, inv);
+    qs_note_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_clover_inverse_odd"); return QS_ECUDA; }
+    return QS_OK;
+}
+
+int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int gamma5, double *work,
+                const double2 *inv)
 {
     const Geom &g = lat->g;
     cudaStream_t st = lat->stream;
@@ -283,8 +401,13 @@ int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int n
     d.gamma5 = 0;
     cudaError_t e = qs_dslash64_parity_launch(d, 1, st);                                     // (D x)_o
     if (e == cudaSuccess) {
-        clover_solve_odd_kernel<<<nbs, 128, 0, st>>>(lat->clov64, (const double2 *)dx, (const double2 *)x,
-                                                     (double2 *)v, g, nrhs, 4.0 + m0);       // v = x - u
+        if (inv)
+            clover_apply_inv_kernel<<<nbs, 128, 0, st>>>(inv, (const double2 *)dx, (const double2 *)x, (double2 *)v,
+                                                         g, nrhs);                             // v = x - u
+        else
+            clover_solve_odd_kernel<<<nbs, 128, 0, st>>>(lat->clov64, (const double2 *)dx, (const double2 *)x,
+                                                         (double2 *)v, g, nrhs, 4.0 + m0);
+
         d.in = v;
         d.out = out;
         d.gamma5 = gamma5;
@@ -320,7 +443,7 @@ extern "C" int qs_apply_Dhat(qs_lattice *lat, double m0, const void *in, void *o
     QS_CUDA(cudaSetDevice(lat->device));
     double *buf = nullptr;
     QS_CUDA(cudaMalloc(&buf, 3 * bytes));
-    int s = qs_dhat_run(lat, m0, (const double *)in, (double *)out, nrhs, gamma5, buf);
+    int s = qs_dhat_run(lat, m0, (const double *)in, (double *)out, nrhs, gamma5, buf, nullptr);
     if (s == QS_OK) {
         const cudaError_t e = cudaStreamSynchronize(lat->stream);
         if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_apply_Dhat"); s = QS_ECUDA; }

@@ -11,7 +11,13 @@ cudaError_t qs_dslash64_parity_launch(const DslashArgs<double> &a, int parity, c
 // D_hat = D_ee - D_eo (D_oo)^-1 D_oe (gamma5 = 1: Q_hat = gamma_5 D_hat) of nrhs FP64 vectors
 // in the canonical layout; odd-site entries of in are ignored, those of out set to zero.
 // Asynchronous on the lattice's stream; work: 3 * nrhs * N_s * 24 doubles; in may equal out.
-int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int gamma5, double *work);
+// inv: NULL (the odd-site blocks are solved on the fly) or the inverses from
+// qs_clover_inverse_odd at the same m0.
+int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int gamma5, double *work,
+                const double2 *inv = nullptr);
+
+// inv = (4 + m0 + A)^-1 on the odd physical sites, [2][6][6][V_phys] complex (asynchronous)
+int qs_clover_inverse_odd(qs_lattice *lat, double m0, double2 *inv);
 
 // out = in on the even sites, 0 on the odd ones (nrhs FP64 vectors, asynchronous)
 int qs_even_mask(qs_lattice *lat, const double *in, double *out, int nrhs);

@@ -358,6 +358,10 @@ struct RwWork {
     double *eta, *t, *x, *r, *p, *ap, *tmp, *dwork;
     double2 *part, *dots;
     double2 host_dots[64];
+    // odd-site block inverses at the two masses of the estimate
+    double mass[2];
+    const double2 *inv[2];
+    const double2 *inv_for(double m) const { return m == mass[0] ? inv[0] : m == mass[1] ? inv[1] : nullptr; }
 };
 
 int rw_check(const char *where)
@@ -385,8 +389,8 @@ unsigned rw_grid(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256
 // out = Q_hat(m)^2 in + sigma in
 int rw_q2(RwWork &w, double m, double sigma, const double *in, double *out)
 {
-    QS_TRY(qs_dhat_run(w.lat, m, in, w.tmp, w.nrhs, 1, w.dwork));
-    QS_TRY(qs_dhat_run(w.lat, m, w.tmp, out, w.nrhs, 1, w.dwork));
+    QS_TRY(qs_dhat_run(w.lat, m, in, w.tmp, w.nrhs, 1, w.dwork, w.inv_for(m)));
+    QS_TRY(qs_dhat_run(w.lat, m, w.tmp, out, w.nrhs, 1, w.dwork, w.inv_for(m)));
     Coef c;
     for (int r = 0; r < w.nrhs; ++r) c.v[r] = sigma;
     rw_axpy<<<dim3(rw_grid(w.len), w.nrhs), 256, 0, w.lat->stream>>>(out, in, c, w.len);
@@ -454,7 +458,7 @@ int rw_shifted_inverse(RwWork &w, double m, double shift, const double *in, doub
     rw_g5<<<rw_grid(nc), 256, 0, st>>>((double2 *)w.t, (const double2 *)in, nc);
     qs_note_launches(1);
     QS_TRY(rw_cg(w, m, shift * shift, w.t, w.x, tol, max_iter, iters));
-    QS_TRY(qs_dhat_run(w.lat, m, w.x, out, w.nrhs, 1, w.dwork));
+    QS_TRY(qs_dhat_run(w.lat, m, w.x, out, w.nrhs, 1, w.dwork, w.inv_for(m)));
     rw_add_ix<<<rw_grid(nc), 256, 0, st>>>((double2 *)out, (const double2 *)out, (const double2 *)w.x, -shift, nc);
     qs_note_launches(1);
     return rw_check("rw_shifted_inverse");
@@ -480,7 +484,9 @@ extern "C" int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const doub
     w.len = g.Ns * 24;
     const int64_t vl = (int64_t)nsrc * w.len;   // doubles per block of nsrc vectors
     double *buf = nullptr;
-    QS_CUDA(cudaMalloc(&buf, 12 * vl * sizeof(double) + (size_t)nsrc * (RW_PARTS + 1) * sizeof(double2)));
+    const size_t inv_len = (size_t)72 * g.Vphys;   // complex entries of the inverses at one mass
+    QS_CUDA(cudaMalloc(&buf, 12 * vl * sizeof(double) + (size_t)nsrc * (RW_PARTS + 1) * sizeof(double2) +
+                                 2 * inv_len * sizeof(double2)));
     w.eta = buf;
     w.t = buf + vl;
     w.x = buf + 2 * vl;
@@ -492,12 +498,19 @@ extern "C" int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const doub
     double *v1 = buf + 10 * vl, *v2 = buf + 11 * vl;
     w.part = (double2 *)(buf + 12 * vl);
     w.dots = w.part + (size_t)nsrc * RW_PARTS;
+    double2 *inv = w.dots + nsrc;
+    w.mass[0] = m;
+    w.mass[1] = mp;
+    w.inv[0] = inv;
+    w.inv[1] = inv + inv_len;
     cudaStream_t st = lat->stream;
     const int64_t nc = vl / 2;
     int s = QS_OK, total_it = 0;
     double lw = 0;
     do {
         if ((s = qs_even_mask(lat, (const double *)eta, w.eta, nsrc)) != QS_OK) break;
+        if ((s = qs_clover_inverse_odd(lat, m, (double2 *)w.inv[0])) != QS_OK) break;
+        if ((s = qs_clover_inverse_odd(lat, mp, (double2 *)w.inv[1])) != QS_OK) break;
         for (int j = 0; j < n && s == QS_OK; ++j) {
             int it = 0;
             // v1 = i gamma_5 (mu - nu) a^-1 eta, v2 = b^-1 v1 = S_j eta
@@ -508,8 +521,8 @@ extern "C" int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const doub
             if ((s = rw_shifted_inverse(w, mp, mu[j], v1, v2, tol, max_iter, &it)) != QS_OK) break;
             total_it += it;
             // v1 = X eta = D_hat(m') S_j eta - D_hat(m) S_j eta
-            if ((s = qs_dhat_run(lat, mp, v2, v1, nsrc, 0, w.dwork)) != QS_OK) break;
-            if ((s = qs_dhat_run(lat, m, v2, w.tmp, nsrc, 0, w.dwork)) != QS_OK) break;
+            if ((s = qs_dhat_run(lat, mp, v2, v1, nsrc, 0, w.dwork, w.inv_for(mp))) != QS_OK) break;
+            if ((s = qs_dhat_run(lat, m, v2, w.tmp, nsrc, 0, w.dwork, w.inv_for(m))) != QS_OK) break;
             Coef c;
             for (int r = 0; r < nsrc; ++r) c.v[r] = -1.0;
             rw_axpy<<<dim3(rw_grid(w.len), nsrc), 256, 0, st>>>(v1, w.tmp, c, w.len);

@@ -143,11 +143,13 @@ def test_checkpoint_resume_and_step_log(qs, tmp_path):
     # so the cut flow leaves a checkpoint beyond the target
     m2 = 0.3
     s_a, rep_a = lat.pfaffian_sign(m2, qs.sign_default_opts(eig=eig))
-    assert rep_a["n"] > 3 and s_a == sign_by_eigencount(op, m2)
-    with pytest.raises(qs.QStarError):
-        lat.pfaffian_sign(m2, qs.sign_default_opts(eig=eig, max_steps=2, checkpoint_path=ck2))
+    assert rep_a["n"] >= 3 and s_a == sign_by_eigencount(op, m2)
+    with pytest.raises(qs.QStarError):     # one step, then the cap
+        lat.pfaffian_sign(m2, qs.sign_default_opts(eig=eig, max_steps=1, checkpoint_path=ck2))
     cut = json.load(open(ck2))
-    assert cut["m"] > m2 and cut["steps"] <= 2 and cut["m"] in rep_a["mass"]
+    # the same first step as the uninterrupted flow, up to the eigensolver's tolerance (the
+    # handle's warm start differs between the runs)
+    assert cut["m"] > m2 and cut["steps"] == 1 and abs(cut["m"] - rep_a["mass"][1]) < 1e-6
     s_res, rep_res = lat.pfaffian_sign(m2, qs.sign_default_opts(eig=eig, checkpoint_path=ck2, resume=1))
     assert s_res == s_a and rep_res["resumed_from"] == cut["m"]
     assert rep_res["mass"][0] == cut["m"]
