@@ -330,7 +330,7 @@ QS_API int qs_ratapprox(int n, double ra, double rb, double *A, double *nu, doub
  * ||r|| <= tol ||b||, at most max_iter iterations (QS_ENOCONV beyond).  q: HOST array of
  * n * nsrc; log_w, cg_iterations (total over all solves): HOST, may be NULL.  Allocates
  * 12 nsrc vectors of work and the odd-site block inverses at m and m' (2 x 1152 bytes per
- * physical site); synchronises the lattice's stream.  QS_EINVAL for odd T or L. */
+ * odd physical site); synchronises the lattice's stream.  QS_EINVAL for odd T or L. */
 QS_API int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const double *nu, const double *mu,
                      const void *eta, int nsrc, double tol, int max_iter, double *q, double *log_w,
                      int *cg_iterations);

@@ -257,8 +257,8 @@ __global__ void clover_solve_odd_kernel(const double *__restrict__ clov, const d
 }
 
 // inv = (4 + m0 + A(x))^-1 for every odd physical site x, both chiral blocks, by Gauss-Jordan
-// elimination with partial pivoting in FP64; layout [block][6][6][V_phys] complex (entries of
-// even sites are left untouched).  The mirror site's block S conj(M) S has the inverse
+// elimination with partial pivoting in FP64; layout [block][6][6][V_phys / 2] complex, the odd
+// physical site p at index p / 2 (L is even, so the odd sites of a row of L alternate).  The mirror site's block S conj(M) S has the inverse
 // S conj(M^-1) S, formed on the fly when it is applied.
 __global__ void clover_inverse_kernel(const double *__restrict__ clov, Geom g, double dm, double2 *__restrict__ inv)
 {
@@ -321,45 +321,50 @@ __global__ void clover_inverse_kernel(const double *__restrict__ clov, Geom g, d
                 }
             }
         }
+        const int64_t V2 = V / 2, q = p >> 1;   // odd sites of a row of L have one index parity each
         for (int i = 0; i < 6; ++i)
-            for (int j = 0; j < 6; ++j) inv[((int64_t)b * 36 + i * 6 + j) * V + p] = make_double2(br[i][j], bi[i][j]);
+            for (int j = 0; j < 6; ++j) inv[((int64_t)b * 36 + i * 6 + j) * V2 + q] = make_double2(br[i][j], bi[i][j]);
     }
 }
 
-// v = x on even sites, v = -(4 + m0 + A(x))^-1 t on odd sites from the stored inverses
+// v = x on even sites, v = -(4 + m0 + A(x))^-1 t on odd sites from the stored inverses.  Thread
+// j takes the j-th odd site (x = 2 jx or 2 jx + 1 in its row) and copies its even x partner.
 __global__ void clover_apply_inv_kernel(const double2 *__restrict__ inv, const double2 *__restrict__ t,
                                         const double2 *__restrict__ xe, double2 *__restrict__ v, Geom g, int k)
 {
-    const int64_t n = g.Ns * k;
+    const int64_t half = g.Ns / 2;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t s = i % g.Ns;
-    double2 *vi = v + i * 12;
-    if (site_parity(g, s) == 0) {
-        const double2 *xi = xe + i * 12;
-        for (int c = 0; c < 12; ++c) vi[c] = xi[c];
-        return;
+    if (i >= half * k) return;
+    const int64_t r = i / half, j = i - r * half;
+    const int64_t row = j / g.L;
+    const int jx = (int)(j - row * g.L);
+    const int y = (int)(row % g.L), z = (int)((row / g.L) % g.L), tt = (int)(row / ((int64_t)g.L * g.L));
+    const int x = 2 * jx + ((1 + tt + z + y) & 1);
+    const int64_t s = row * g.L2 + x;
+    {
+        const int64_t e = (r * g.Ns + (s ^ 1)) * 12;
+        for (int c = 0; c < 12; ++c) v[e + c] = xe[e + c];
     }
-    const double2 *ti = t + i * 12;
-    const int x = (int)(s % g.L2);
+    const double2 *ti = t + (r * g.Ns + s) * 12;
+    double2 *vi = v + (r * g.Ns + s) * 12;
     const bool mir = x >= g.L;
-    const int64_t p = (s / g.L2) * g.L + (mir ? x - g.L : x);
-    const int64_t V = g.Vphys;
+    const int64_t p = row * g.L + (mir ? x - g.L : x);
+    const int64_t V2 = g.Vphys / 2, q = p >> 1;
     for (int b = 0; b < 2; ++b)
-        for (int r = 0; r < 6; ++r) {
+        for (int rr = 0; rr < 6; ++rr) {
             double accr = 0, acci = 0;
             for (int c = 0; c < 6; ++c) {
-                const int ii = mir ? (r + 3) % 6 : r, jj = mir ? (c + 3) % 6 : c;
-                double2 e = inv[((int64_t)b * 36 + ii * 6 + jj) * V + p];
+                const int ii = mir ? (rr + 3) % 6 : rr, jj = mir ? (c + 3) % 6 : c;
+                double2 e = inv[((int64_t)b * 36 + ii * 6 + jj) * V2 + q];
                 if (mir) {
                     e.y = -e.y;
-                    if ((r < 3) != (c < 3)) { e.x = -e.x; e.y = -e.y; }
+                    if ((rr < 3) != (c < 3)) { e.x = -e.x; e.y = -e.y; }
                 }
-                const double2 q = ti[6 * b + c];
-                accr += e.x * q.x - e.y * q.y;
-                acci += e.x * q.y + e.y * q.x;
+                const double2 w = ti[6 * b + c];
+                accr += e.x * w.x - e.y * w.y;
+                acci += e.x * w.y + e.y * w.x;
             }
-            vi[6 * b + r] = make_double2(-accr, -acci);
+            vi[6 * b + rr] = make_double2(-accr, -acci);
         }
 }
 
@@ -402,8 +407,8 @@ int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int n
     cudaError_t e = qs_dslash64_parity_launch(d, 1, st);                                     // (D x)_o
     if (e == cudaSuccess) {
         if (inv)
-            clover_apply_inv_kernel<<<nbs, 128, 0, st>>>(inv, (const double2 *)dx, (const double2 *)x, (double2 *)v,
-                                                         g, nrhs);                             // v = x - u
+            clover_apply_inv_kernel<<<(unsigned)((g.Ns / 2 * nrhs + 127) / 128), 128, 0, st>>>(
+                inv, (const double2 *)dx, (const double2 *)x, (double2 *)v, g, nrhs);          // v = x - u
         else
             clover_solve_odd_kernel<<<nbs, 128, 0, st>>>(lat->clov64, (const double2 *)dx, (const double2 *)x,
                                                          (double2 *)v, g, nrhs, 4.0 + m0);

@@ -16,7 +16,8 @@ cudaError_t qs_dslash64_parity_launch(const DslashArgs<double> &a, int parity, c
 int qs_dhat_run(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int gamma5, double *work,
                 const double2 *inv = nullptr);
 
-// inv = (4 + m0 + A)^-1 on the odd physical sites, [2][6][6][V_phys] complex (asynchronous)
+// inv = (4 + m0 + A)^-1 on the odd physical sites, [2][6][6][V_phys / 2] complex, the odd
+// physical site p at index p / 2 (asynchronous)
 int qs_clover_inverse_odd(qs_lattice *lat, double m0, double2 *inv);
 
 // out = in on the even sites, 0 on the odd ones (nrhs FP64 vectors, asynchronous)

@@ -484,7 +484,7 @@ extern "C" int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const doub
     w.len = g.Ns * 24;
     const int64_t vl = (int64_t)nsrc * w.len;   // doubles per block of nsrc vectors
     double *buf = nullptr;
-    const size_t inv_len = (size_t)72 * g.Vphys;   // complex entries of the inverses at one mass
+    const size_t inv_len = (size_t)36 * g.Vphys;   // complex entries of the inverses at one mass
     QS_CUDA(cudaMalloc(&buf, 12 * vl * sizeof(double) + (size_t)nsrc * (RW_PARTS + 1) * sizeof(double2) +
                                  2 * inv_len * sizeof(double2)));
     w.eta = buf;
