@@ -22,7 +22,6 @@
 #include "evenodd.cuh"
 
 #include <math.h>
-#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -357,7 +356,6 @@ struct RwWork {
     int64_t len;          // doubles per vector
     double *eta, *t, *x, *r, *p, *ap, *tmp, *dwork;
     double2 *part, *dots;
-    double2 host_dots[64];
     // odd-site block inverses at the two masses of the estimate
     double mass[2];
     const double2 *inv[2];
