@@ -335,6 +335,17 @@ QS_API int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const double *
                      const void *eta, int nsrc, double tol, int max_iter, double *q, double *log_w,
                      int *cg_iterations);
 
+/* qs_solve_D: x = D(m0)^-1 b in FP64.  even_odd = 1: the even-odd preconditioned solve of
+ * Sec. 4 -- b'_e = b_e - D_eo (D_oo)^-1 b_o, D_hat x_e = b'_e by conjugate gradients on
+ * Q_hat^2 (half the sites, better conditioned), x_o = (D_oo)^-1 (b_o - D_oe x_e); requires even
+ * T and L.  even_odd = 0: conjugate gradients on the full-lattice Q^2 (for comparison).
+ * b, x: DEVICE buffers of nrhs <= 64 FP64 spinors, canonical layout, not overlapping.  The CG
+ * stops at ||r|| <= tol ||rhs|| for every right-hand side (QS_ENOCONV after max_iter);
+ * *iterations (may be NULL) gets the count.  Allocates 11 nrhs vectors of work (plus the
+ * odd-site inverses, 1152 bytes per odd physical site); synchronises the stream. */
+QS_API int qs_solve_D(qs_lattice *lat, double m0, const void *b, void *x, int nrhs, int even_odd, double tol,
+                      int max_iter, int *iterations);
+
 /* The bounds step A takes from one block of Ritz pairs (host arithmetic, no GPU work):
  * *lambda_bar = min |theta_j| and *lo = min (|theta_j| - res_j) over the values that carry
  * information: the first nwant (the converged ones) and every other one with

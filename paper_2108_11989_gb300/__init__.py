@@ -134,6 +134,7 @@ def _load():
         "qs_apply_Dhat": (I, [P, D, P, P, I, I]),
         "qs_block_bounds": (I, [P, P, I, I, P, P]),
         "qs_ratapprox": (I, [I, D, D, P, P, P, P]),
+        "qs_solve_D": (I, [P, D, P, P, I, I, D, I, P]),
         "qs_w_mass": (I, [P, D, D, I, P, P, P, I, D, I, P, P, P]),
         "qs_apply_Q_norm2_noalloc": (I, [P, D, P, P, I, I, P]),
         "qs_strerror": (ctypes.c_char_p, [I]),
@@ -320,6 +321,17 @@ def block_bounds(theta, res, nwant):
     _check(_lib.qs_block_bounds(th.ctypes.data, rs.ctypes.data, th.size, int(nwant), ctypes.byref(lb),
                                 ctypes.byref(lo)), "block_bounds")
     return lb.value, lo.value
+
+
+def solve_D(h, m0, b, x, even_odd=True, tol=1e-10, max_iter=20000):
+    """qs_solve_D: x = D(m0)^-1 b (float64 device spinors); returns the CG iterations."""
+    import torch
+    if b.dtype != torch.float64 or x.dtype != torch.float64 or b.shape != x.shape:
+        raise TypeError("solve_D takes two float64 spinor tensors of one shape")
+    it = ctypes.c_int()
+    _check(_lib.qs_solve_D(h, float(m0), b.data_ptr(), x.data_ptr(), _nrhs(h, b), int(bool(even_odd)), float(tol),
+                           int(max_iter), ctypes.byref(it)), "solve_D")
+    return it.value
 
 
 def ratapprox(n, ra, rb):
@@ -532,6 +544,9 @@ class Lattice:
 
     def apply_Dhat(self, m0, inp, out, gamma5=False):
         apply_Dhat(self.h, m0, inp, out, gamma5)
+
+    def solve_D(self, m0, b, x, even_odd=True, tol=1e-10, max_iter=20000):
+        return solve_D(self.h, m0, b, x, even_odd, tol, max_iter)
 
     def w_mass(self, m, mp, nu, mu, eta, tol=1e-10, max_iter=20000):
         return w_mass(self.h, m, mp, nu, mu, eta, tol, max_iter)

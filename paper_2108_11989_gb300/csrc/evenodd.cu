@@ -368,6 +368,47 @@ __global__ void clover_apply_inv_kernel(const double2 *__restrict__ inv, const d
         }
 }
 
+// out = scale (4 + m0 + A(x))^-1 t on odd sites (stored inverses), 0 on even sites; thread j
+// takes the j-th odd site and zeroes its even x partner
+__global__ void oo_inverse_kernel(const double2 *__restrict__ inv, const double2 *__restrict__ t,
+                                  double2 *__restrict__ out, Geom g, int k, double scale)
+{
+    const int64_t half = g.Ns / 2;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= half * k) return;
+    const int64_t r = i / half, j = i - r * half;
+    const int64_t row = j / g.L;
+    const int jx = (int)(j - row * g.L);
+    const int y = (int)(row % g.L), z = (int)((row / g.L) % g.L), tt = (int)(row / ((int64_t)g.L * g.L));
+    const int x = 2 * jx + ((1 + tt + z + y) & 1);
+    const int64_t s = row * g.L2 + x;
+    {
+        double2 *o = out + (r * g.Ns + (s ^ 1)) * 12;
+        for (int c = 0; c < 12; ++c) o[c] = make_double2(0.0, 0.0);
+    }
+    const double2 *ti = t + (r * g.Ns + s) * 12;
+    double2 *oi = out + (r * g.Ns + s) * 12;
+    const bool mir = x >= g.L;
+    const int64_t p = row * g.L + (mir ? x - g.L : x);
+    const int64_t V2 = g.Vphys / 2, q = p >> 1;
+    for (int b = 0; b < 2; ++b)
+        for (int rr = 0; rr < 6; ++rr) {
+            double accr = 0, acci = 0;
+            for (int c = 0; c < 6; ++c) {
+                const int ii = mir ? (rr + 3) % 6 : rr, jj = mir ? (c + 3) % 6 : c;
+                double2 e = inv[((int64_t)b * 36 + ii * 6 + jj) * V2 + q];
+                if (mir) {
+                    e.y = -e.y;
+                    if ((rr < 3) != (c < 3)) { e.x = -e.x; e.y = -e.y; }
+                }
+                const double2 w = ti[6 * b + c];
+                accr += e.x * w.x - e.y * w.y;
+                acci += e.x * w.y + e.y * w.x;
+            }
+            oi[6 * b + rr] = make_double2(scale * accr, scale * acci);
+        }
+}
+
 }  // namespace
 
 // D_hat (or Q_hat) of nrhs FP64 vectors, asynchronous on the lattice's stream; work holds
@@ -375,6 +416,34 @@ __global__ void clover_apply_inv_kernel(const double2 *__restrict__ inv, const d
 // With x the even part of the input, u = (D_oo)^-1 (D x)_o and v = x - u (even part x,
 // odd part -u):  D_hat x = (D x)_e - (D u)_e = (D v)_e, so the operator is applied twice,
 // each time on the output sites of one parity only.
+int qs_oo_inverse_apply(qs_lattice *lat, const double2 *inv, const double *in, double *out, int nrhs, double scale)
+{
+    const int64_t n = lat->g.Ns / 2 * nrhs;
+    oo_inverse_kernel<<<(unsigned)((n + 127) / 128), 128, 0, lat->stream>>>(inv, (const double2 *)in, (double2 *)out,
+                                                                          lat->g, nrhs, scale);
+    qs_note_launches(1);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_oo_inverse_apply"); return QS_ECUDA; }
+    return QS_OK;
+}
+
+int qs_dslash64_parity(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int parity)
+{
+    DslashArgs<double> d;
+    d.g = lat->g;
+    d.links = lat->links64;
+    d.clov = lat->clov64;
+    d.nrhs = nrhs;
+    for (int r = 0; r < nrhs; ++r) d.m0[r] = m0;
+    d.in = in;
+    d.out = out;
+    d.gamma5 = 0;
+    const cudaError_t e = qs_dslash64_parity_launch(d, parity, lat->stream);
+    qs_note_launches(1);
+    if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_dslash64_parity"); return QS_ECUDA; }
+    return QS_OK;
+}
+
 int qs_clover_inverse_odd(qs_lattice *lat, double m0, double2 *inv)
 {
     const int64_t V = lat->g.Vphys;

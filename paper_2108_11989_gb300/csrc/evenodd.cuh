@@ -22,3 +22,10 @@ int qs_clover_inverse_odd(qs_lattice *lat, double m0, double2 *inv);
 
 // out = in on the even sites, 0 on the odd ones (nrhs FP64 vectors, asynchronous)
 int qs_even_mask(qs_lattice *lat, const double *in, double *out, int nrhs);
+
+// out = scale (D_oo)^-1 in on the odd sites (inverses from qs_clover_inverse_odd), 0 on the
+// even sites (asynchronous; in and out must not overlap)
+int qs_oo_inverse_apply(qs_lattice *lat, const double2 *inv, const double *in, double *out, int nrhs, double scale);
+
+// out = D in on the output sites of one parity, 0 on the others (FP64, asynchronous)
+int qs_dslash64_parity(qs_lattice *lat, double m0, const double *in, double *out, int nrhs, int parity);

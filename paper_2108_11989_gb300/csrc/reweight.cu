@@ -356,6 +356,7 @@ struct RwWork {
     int64_t len;          // doubles per vector
     double *eta, *t, *x, *r, *p, *ap, *tmp, *dwork;
     double2 *part, *dots;
+    int full;             // 1: Q^2 of the full-lattice operator instead of Q_hat^2
     // odd-site block inverses at the two masses of the estimate
     double mass[2];
     const double2 *inv[2];
@@ -387,8 +388,15 @@ unsigned rw_grid(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256
 // out = Q_hat(m)^2 in + sigma in
 int rw_q2(RwWork &w, double m, double sigma, const double *in, double *out)
 {
-    QS_TRY(qs_dhat_run(w.lat, m, in, w.tmp, w.nrhs, 1, w.dwork, w.inv_for(m)));
-    QS_TRY(qs_dhat_run(w.lat, m, w.tmp, out, w.nrhs, 1, w.dwork, w.inv_for(m)));
+    if (w.full) {
+        double mm[64];
+        for (int r = 0; r < w.nrhs; ++r) mm[r] = m;
+        QS_TRY(qs_dslash_run(w.lat, QS_F64, mm, in, w.tmp, w.nrhs, 1, 0));
+        QS_TRY(qs_dslash_run(w.lat, QS_F64, mm, w.tmp, out, w.nrhs, 1, 0));
+    } else {
+        QS_TRY(qs_dhat_run(w.lat, m, in, w.tmp, w.nrhs, 1, w.dwork, w.inv_for(m)));
+        QS_TRY(qs_dhat_run(w.lat, m, w.tmp, out, w.nrhs, 1, w.dwork, w.inv_for(m)));
+    }
     Coef c;
     for (int r = 0; r < w.nrhs; ++r) c.v[r] = sigma;
     rw_axpy<<<dim3(rw_grid(w.len), w.nrhs), 256, 0, w.lat->stream>>>(out, in, c, w.len);
@@ -478,6 +486,7 @@ extern "C" int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const doub
     QS_CUDA(cudaSetDevice(lat->device));
     RwWork w;
     w.lat = lat;
+    w.full = 0;
     w.nrhs = nsrc;
     w.len = g.Ns * 24;
     const int64_t vl = (int64_t)nsrc * w.len;   // doubles per block of nsrc vectors
@@ -542,5 +551,96 @@ extern "C" int qs_w_mass(qs_lattice *lat, double m, double mp, int n, const doub
     cudaFree(buf);
     if (cg_iterations) *cg_iterations = total_it;
     if (s == QS_OK && log_w) *log_w = lw;
+    return s;
+}
+
+// ---- the even-odd preconditioned solve of D x = b (Sec. 4) ---------------------------------
+namespace {
+int rw_copy(void *dst, const void *src, size_t bytes, cudaStream_t st)
+{
+    const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_solve_D copy"); return QS_ECUDA; }
+    return QS_OK;
+}
+}  // namespace
+
+// even_odd = 1:  b'_e = b_e - D_eo (D_oo)^-1 b_o;  D_hat x_e = b'_e by CG on Q_hat^2
+// (x_e = Q_hat (Q_hat^2)^-1 gamma_5 b'_e);  x_o = (D_oo)^-1 (b_o - D_oe x_e).
+// even_odd = 0:  x = Q (Q^2)^-1 gamma_5 b by CG on the full-lattice Q^2 (the comparison).
+extern "C" int qs_solve_D(qs_lattice *lat, double m0, const void *b, void *x, int nrhs, int even_odd, double tol,
+                          int max_iter, int *iterations)
+{
+    if (!lat || !b || !x || nrhs < 1 || nrhs > 64 || !(tol > 0) || max_iter < 1) return QS_EINVAL;
+    if (((uintptr_t)b | (uintptr_t)x) & 15) return QS_EINVAL;
+    if (!lat->gauge_loaded) return QS_EINVAL;
+    const Geom &g = lat->g;
+    if (even_odd && ((g.T | g.L) & 1)) return QS_EINVAL;
+    const size_t bytes = (size_t)nrhs * g.Ns * 24 * sizeof(double);
+    const char *pa = (const char *)b, *pb = (const char *)x;
+    if (pa < pb + bytes && pb < pa + bytes) return QS_EINVAL;
+    QS_CUDA(cudaSetDevice(lat->device));
+    RwWork w;
+    w.lat = lat;
+    w.full = even_odd ? 0 : 1;
+    w.nrhs = nrhs;
+    w.len = g.Ns * 24;
+    const int64_t vl = (int64_t)nrhs * w.len;
+    const size_t inv_len = even_odd ? (size_t)36 * g.Vphys : 0;
+    double *buf = nullptr;
+    QS_CUDA(cudaMalloc(&buf, 11 * vl * sizeof(double) + (size_t)nrhs * (RW_PARTS + 1) * sizeof(double2) +
+                                 inv_len * sizeof(double2)));
+    w.eta = nullptr;
+    w.t = buf;
+    w.x = buf + vl;
+    w.r = buf + 2 * vl;
+    w.p = buf + 3 * vl;
+    w.ap = buf + 4 * vl;
+    w.tmp = buf + 5 * vl;
+    w.dwork = buf + 6 * vl;   // 3 blocks
+    double *a1 = buf + 9 * vl, *a2 = buf + 10 * vl;
+    w.part = (double2 *)(buf + 11 * vl);
+    w.dots = w.part + (size_t)nrhs * RW_PARTS;
+    double2 *inv = even_odd ? w.dots + nrhs : nullptr;
+    w.mass[0] = w.mass[1] = m0;
+    w.inv[0] = w.inv[1] = inv;
+    cudaStream_t st = lat->stream;
+    const int64_t nc = vl / 2;
+    Coef minus, plus;
+    for (int r = 0; r < nrhs; ++r) { minus.v[r] = -1.0; plus.v[r] = 1.0; }
+    const dim3 ga(rw_grid(w.len), nrhs);
+    int s = QS_OK, it = 0;
+    do {
+        if (even_odd) {
+            if ((s = qs_clover_inverse_odd(lat, m0, inv)) != QS_OK) break;
+            if ((s = qs_oo_inverse_apply(lat, inv, (const double *)b, a1, nrhs, 1.0)) != QS_OK) break;
+            if ((s = qs_dslash64_parity(lat, m0, a1, a2, nrhs, 0)) != QS_OK) break;   // D_eo D_oo^-1 b_o
+            if ((s = qs_even_mask(lat, (const double *)b, w.t, nrhs)) != QS_OK) break;
+            rw_axpy<<<ga, 256, 0, st>>>(w.t, a2, minus, w.len);                          // b'_e
+            rw_g5<<<rw_grid(nc), 256, 0, st>>>((double2 *)w.t, (const double2 *)w.t, nc);
+            qs_note_launches(2);
+            if ((s = rw_cg(w, m0, 0.0, w.t, w.x, tol, max_iter, &it)) != QS_OK) break;
+            if ((s = qs_dhat_run(lat, m0, w.x, a1, nrhs, 1, w.dwork, inv)) != QS_OK) break;   // x_e
+            if ((s = qs_dslash64_parity(lat, m0, a1, a2, nrhs, 1)) != QS_OK) break;            // D_oe x_e
+            if ((s = rw_copy(w.t, b, bytes, st)) != QS_OK) break;
+            rw_axpy<<<ga, 256, 0, st>>>(w.t, a2, minus, w.len);                          // b_o - D_oe x_e
+            qs_note_launches(1);
+            if ((s = qs_oo_inverse_apply(lat, inv, w.t, a2, nrhs, 1.0)) != QS_OK) break;     // x_o
+            if ((s = rw_copy(x, a1, bytes, st)) != QS_OK) break;
+            rw_axpy<<<ga, 256, 0, st>>>((double *)x, a2, plus, w.len);
+            qs_note_launches(1);
+        } else {
+            rw_g5<<<rw_grid(nc), 256, 0, st>>>((double2 *)w.t, (const double2 *)b, nc);
+            qs_note_launches(1);
+            if ((s = rw_cg(w, m0, 0.0, w.t, w.x, tol, max_iter, &it)) != QS_OK) break;
+            double mm[64];
+            for (int r = 0; r < nrhs; ++r) mm[r] = m0;
+            if ((s = qs_dslash_run(lat, QS_F64, mm, w.x, x, nrhs, 1, 0)) != QS_OK) break;    // x = Q y
+        }
+        if ((s = rw_check("qs_solve_D")) != QS_OK) break;
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { qs_record_cuda_error(e, "qs_solve_D"); s = QS_ECUDA; }
+    } while (0);
+    cudaFree(buf);
+    if (iterations) *iterations = it;
     return s;
 }
