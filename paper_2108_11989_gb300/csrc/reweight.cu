@@ -1,4 +1,4 @@
-// Mass reweighting (Sec. 4).
+// Mass reweighting and the even-odd preconditioned solve (Sec. 4).
 //
 // qs_ratapprox: the (n, n) rational function R(y) = A prod_i (y + nu_i^2) / (y + mu_i^2) of
 // least uniform relative error |R(y) y^(1/4) - 1| on y in [r_a^2, r_b^2] (eq. ratapprox; R
@@ -19,6 +19,9 @@
 // inverse by FP64 conjugate gradients on the positive operator Q_hat^2 + nu^2.  The estimate
 // is prod_j (1/N) sum_l exp(-q_jl) (E[exp(-(eta, R_j eta))] = 1/det(1 + R_j) for sources of
 // density ~ exp(-(eta, eta))).
+//
+// qs_solve_D: x = D^-1 b through the Schur complement on the even sites, with the same FP64
+// CG (on Q_hat^2) and the odd-site inverses; or, for comparison, CG on the full-lattice Q^2.
 #include "evenodd.cuh"
 
 #include <math.h>
