@@ -43,6 +43,9 @@ def test_equioscillation_at_higher_order(qs, n, ratio):
     assert np.max(ext) == pytest.approx(d, rel=1e-6)
     assert np.min(ext) >= d * (1 - 1e-6)
     assert np.all(np.diff(nu) > 0) and np.all(np.diff(mu) > 0)
+    # zeros and poles interlace on the negative axis, mu_1 < nu_1 < mu_2 < ... (R decreases)
+    lab = np.concatenate([np.zeros(n), np.ones(n)])[np.argsort(np.concatenate([mu, nu]))]
+    assert np.all(lab[0::2] == 0) and np.all(lab[1::2] == 1)
 
 
 def test_rejects_bad_arguments(qs):
