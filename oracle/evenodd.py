@@ -15,8 +15,9 @@ from the dense D, and ``schur_det`` the identity det D = det D^oo det D_hat.
 Pins (tests/test_oracle_evenodd.py): the odd-odd part of the dense D has no entries
 between different sites; the dense slogdet of that part equals ``log_det_oo``; the
 Schur identity det D = det D^oo det D_hat holds on a rough field; the free field gives
-the closed form log|det D^oo| = 12 N_odd log|4 + m0|; on the free field D_hat x equals
-(4 + m0) x - H^2 x / (4 + m0) with H the hopping part, applied by the matrix-free operator.
+the closed form log|det D^oo| = 12 N_odd log|4 + m0|; on the free field D_hat equals
+(4 + m0) - H_eo H_oe / (4 + m0) with H the hopping part of the dense D; the block-elimination
+identity D y = (b_e, 0) => D_hat y_e = b_e; gamma_5 D_hat is Hermitian.
 """
 import numpy as np
 

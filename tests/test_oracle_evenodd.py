@@ -58,3 +58,20 @@ def test_qhat_is_hermitian(rough):
     Dhat, _ = dhat_dense(rough, 0.1)
     assert np.max(np.abs(Qhat - Qhat.conj().T)) < 1e-12 * np.abs(Qhat).max()
     assert np.max(np.abs(Dhat - Dhat.conj().T)) > 1e-3 * np.abs(Dhat).max()   # D_hat itself is not
+
+
+def test_dhat_free_field_closed_form():
+    # free field: A = 0, so D_oo = (4 + m0) and D_hat = (4 + m0) - H_eo H_oe / (4 + m0),
+    # H the hopping part of D (D minus its diagonal), formed here without any inverse
+    T, L = 4, 2
+    op = WilsonDirac(GaugeConfig(T, L, unit_su3_field(T, L), None, 1.9, 1.0))
+    m0 = -0.3
+    D = op.dense_D(m0)
+    H = D - (4.0 + m0) * np.eye(D.shape[0])
+    p = np.repeat(parity(op.lat), 12)
+    e, o = np.nonzero(p == 0)[0], np.nonzero(p == 1)[0]
+    assert np.max(np.abs(H[np.ix_(e, e)])) == 0 and np.max(np.abs(H[np.ix_(o, o)])) == 0
+    closed = (4.0 + m0) * np.eye(len(e)) - H[np.ix_(e, o)] @ H[np.ix_(o, e)] / (4.0 + m0)
+    Dhat, e2 = dhat_dense(op, m0)
+    assert np.array_equal(e, e2)
+    assert np.max(np.abs(Dhat - closed)) < 1e-13
